@@ -1,0 +1,133 @@
+"""TFIM system Hamiltonian, schedule and instantaneous eigenstructure.
+
+Test infrastructure only (see the package docstring).
+
+Sec. V, Eq. H_S: H_S(s) = A(s) H^X + B(s) H^Z with H^X = -sum_i sx_i and (in the
+explicit-sign form used by this library) H^Z = sum_i hz_i sz_i + sum_{i<j} J_ij sz_i sz_j.
+Basis: index x = sum_i bit_i 2^i, qubit i <-> bit i, bit 0 <-> sz = +1.
+
+Sec. II, Eq. Lindblad2: the Lindblad operators are built from the instantaneous
+eigenstates and group level pairs by equal Bohr frequency. Readings (the paper
+states exact equality only):
+  * levels are sorted ascending; consecutive eigenvalues closer than
+    tol = 1e-9 * max(1, max|eps|) form one degenerate manifold, whose energy is
+    the mean of its eigenvalues;
+  * the Bohr frequency of a level pair (a, b) is E(m(b)) - E(m(a)); pairs in the
+    same manifold have omega = 0;
+  * Bohr frequencies of distinct manifold pairs are sorted and chained where
+    consecutive values differ by at most tol; a chain wider than tol is an
+    ambiguous grouping and is rejected.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SX = np.array([[0.0, 1.0], [1.0, 0.0]])
+SZ = np.array([[1.0, 0.0], [0.0, -1.0]])
+
+
+def op_on(qubit: int, op: np.ndarray, n: int) -> np.ndarray:
+    """Dense operator acting as ``op`` on ``qubit`` and identity elsewhere.
+    np.kron puts its first factor on the most significant index bits, so the
+    factors run from qubit n-1 down to qubit 0."""
+    out = np.array([[1.0]])
+    for q in range(n - 1, -1, -1):
+        out = np.kron(out, op if q == qubit else np.eye(2))
+    return out
+
+
+def hamiltonian_terms(inst):
+    """(H^X, H^Z) as dense real matrices (Sec. V, Eq. H_S)."""
+    n = inst.n_qubits
+    HX = -sum(op_on(i, SX, n) for i in range(n))
+    HZ = sum(inst.hz[i] * op_on(i, SZ, n) for i in range(n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            if inst.J[i, j] != 0.0:
+                HZ = HZ + inst.J[i, j] * (op_on(i, SZ, n) @ op_on(j, SZ, n))
+    return HX, HZ
+
+
+def sigma_z_diagonals(n: int) -> np.ndarray:
+    """(n, 2^n) diagonals of sz_alpha, the system-bath coupling operators A_alpha
+    (Sec. V, Eq. SBm: independent sz coupling per qubit)."""
+    return np.array([np.diag(op_on(a, SZ, n)) for a in range(n)])
+
+
+def schedule(inst, s: float):
+    """Piecewise-linear A(s), B(s) through the instance's knots."""
+    return (float(np.interp(s, inst.sched_s, inst.sched_A)),
+            float(np.interp(s, inst.sched_s, inst.sched_B)))
+
+
+def grid(inst):
+    """s_k = k / (K - 1), k = 0..K-1, and the time step dt = t_f / (K - 1)."""
+    K = inst.n_grid
+    return np.arange(K) / (K - 1), inst.t_f / (K - 1)
+
+
+def energy_tol(evals: np.ndarray) -> float:
+    return 1e-9 * max(1.0, float(np.max(np.abs(evals))))
+
+
+class Eigen:
+    """Instantaneous eigensystem of H_S(s) with its degenerate manifolds."""
+
+    def __init__(self, H: np.ndarray):
+        evals, V = np.linalg.eigh(H)
+        self.evals = evals
+        self.V = V
+        self.tol = energy_tol(evals)
+        groups = [[0]]
+        for a in range(1, len(evals)):
+            if evals[a] - evals[a - 1] <= self.tol:
+                groups[-1].append(a)
+            else:
+                groups.append([a])
+        self.manifolds = [np.array(g) for g in groups]
+        self.E = np.array([evals[g].mean() for g in self.manifolds])
+        self.level_manifold = np.empty(len(evals), dtype=int)
+        for m, g in enumerate(self.manifolds):
+            self.level_manifold[g] = m
+        # Bohr frequency of level pair (b -> a): omega[a, b] = E(m(b)) - E(m(a)).
+        El = self.E[self.level_manifold]
+        self.omega = El[None, :] - El[:, None]
+
+    @property
+    def nondegenerate(self) -> bool:
+        return len(self.manifolds) == len(self.evals)
+
+
+def eigen_at(inst, s: float, terms=None) -> Eigen:
+    HX, HZ = terms if terms is not None else hamiltonian_terms(inst)
+    A, B = schedule(inst, s)
+    return Eigen(A * HX + B * HZ)
+
+
+def bohr_classes(eig: Eigen):
+    """Group the manifold pairs (ma, mb), ma != mb, into classes of equal Bohr
+    frequency omega = E(mb) - E(ma) (Sec. II, Eq. Lindblad2).
+
+    Returns a list of (omega, [(ma, mb), ...]); the omega = 0 class, made of all
+    (m, m) pairs, comes first.
+    """
+    nm = len(eig.E)
+    pairs = [(eig.E[mb] - eig.E[ma], ma, mb) for ma in range(nm) for mb in range(nm) if ma != mb]
+    pairs.sort()
+    classes = [(0.0, [(m, m) for m in range(nm)])]
+    cur = []
+    for w, ma, mb in pairs:
+        if cur and w - cur[-1][0] > eig.tol:
+            classes.append(_close_chain(cur, eig.tol))
+            cur = []
+        cur.append((w, ma, mb))
+    if cur:
+        classes.append(_close_chain(cur, eig.tol))
+    return classes
+
+
+def _close_chain(chain, tol):
+    ws = [w for w, _, _ in chain]
+    if ws[-1] - ws[0] > tol:
+        raise ValueError("ambiguous Bohr-frequency grouping: chain wider than tolerance")
+    return (float(np.mean(ws)), [(ma, mb) for _, ma, mb in chain])

@@ -1,0 +1,161 @@
+"""Serial quantum-jump trajectory sampler for the AME (waiting-time algorithm).
+
+Test infrastructure only (see the package docstring).
+
+Sec. IV (simulation procedure) with App. C (waiting times for time-dependent
+operators): draw r; propagate the unnormalised state under H_eff until its
+squared norm has fallen to r; choose the jump from the probabilities
+Pi_i = <A_i^dag A_i> / lambda (App. B.1, Eq. Pi(t)); apply it (Eq. jump),
+renormalise, draw a new r and continue.
+
+Readings shared with the CUDA path:
+  * the state lives in the computational basis here; the generator is frozen
+    on the same symmetric split as the density-matrix oracle (see ``ame``), and
+    each frozen piece is propagated with scipy's matrix exponential of
+    -i H_eff t, H_eff = V K V^T;
+  * the jump time inside a piece is the root of ||exp(-i H_eff t) psi||^2 = r,
+    bracketed and solved by Brent's method; a tie (norm equal to r) jumps;
+  * jump choice with two uniforms (u1, u2). Units (alpha, m, a): qubit alpha,
+    source manifold m, target level a, with weight
+        w = gamma(E(m) - E(m(a))) |sum_{b in m} M_alpha[a,b] c_b|^2 ,  c = V^T psi .
+    Stage one picks (alpha, m) by inverse CDF over alpha ascending, then m
+    ascending in energy, with u1; stage two picks a, ascending, with u2. The
+    class containing (a, m) is the channel; the sum of its units' weights is
+    <A^dag A>, so each channel is drawn with probability Pi_i exactly. The new
+    state is A_{alpha,class} psi, normalised;
+  * random numbers come from ``philox`` with the stream layout stated there.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy import linalg, optimize
+
+from . import ame, lindblad, model, philox
+
+
+class Piece:
+    """No-jump propagation data of one frozen generator."""
+
+    def __init__(self, fr: lindblad.Frame, tau: float):
+        self.fr = fr
+        V = fr.eig.V
+        self.Heff = V @ fr.K @ V.T
+        self.U_tau = linalg.expm(-1j * self.Heff * tau)
+
+    def U(self, t: float):
+        return linalg.expm(-1j * self.Heff * t)
+
+
+def choose_jump(fr: lindblad.Frame, psi: np.ndarray, u1: float, u2: float):
+    """Stage-one and stage-two draws; returns (alpha, m, a, class id, new psi)."""
+    eig = fr.eig
+    c = eig.V.T @ psi
+    n = fr.M.shape[0]
+    nm = len(eig.manifolds)
+    lm = eig.level_manifold
+    W = np.zeros((n, nm))
+    unit_w = {}
+    for al in range(n):
+        for m, lev in enumerate(eig.manifolds):
+            y = fr.M[al][:, lev] @ c[lev]
+            w = fr.gam[:, lev[0]] * np.abs(y) ** 2
+            unit_w[(al, m)] = w
+            W[al, m] = w.sum()
+    flat = W.reshape(-1)
+    cdf = np.cumsum(flat)
+    idx = int(np.searchsorted(cdf, u1 * cdf[-1], side="right"))
+    idx = min(idx, len(flat) - 1)
+    while flat[idx] <= 0.0 and idx > 0:   # rounding guard: never pick an empty unit
+        idx -= 1
+    al, m = divmod(idx, nm)
+    w = unit_w[(al, m)]
+    cdf2 = np.cumsum(w)
+    a = int(np.searchsorted(cdf2, u2 * cdf2[-1], side="right"))
+    a = min(a, len(w) - 1)
+    while w[a] <= 0.0 and a > 0:
+        a -= 1
+    b0 = eig.manifolds[m][0]
+    cls = fr.class_of_pair[a, b0]
+    mask = fr.class_of_pair == cls
+    A = np.where(mask, fr.R[al], 0.0)
+    newc = A @ c
+    newc /= np.linalg.norm(newc)
+    return al, m, a, cls, eig.V @ newc
+
+
+class Trajectory:
+    def __init__(self, traj: int, seed: int, psi0: np.ndarray):
+        self.traj = traj
+        self.seed = seed
+        self.psi = psi0.astype(complex)
+        self.r = philox.first_threshold(seed, traj)
+        self.n_jumps = 0
+        self.jumps = []
+
+    def advance(self, piece: Piece, tau: float, t0: float, grid_index: int, half: int):
+        """Propagate through one frozen piece of length tau starting at t0."""
+        psi = self.psi
+        elapsed = 0.0
+        remaining = tau
+        while True:
+            U = piece.U_tau if elapsed == 0.0 else piece.U(remaining)
+            trial = U @ psi
+            if np.vdot(trial, trial).real > self.r:
+                self.psi = trial
+                return
+            start = psi
+            f = lambda t: np.vdot(v := piece.U(t) @ start, v).real - self.r  # noqa: E731
+            if f(remaining) > 0.0:   # rounding between the two evaluations
+                self.psi = trial
+                return
+            tstar = optimize.brentq(f, 0.0, remaining, xtol=1e-16 * max(tau, 1e-30), rtol=1e-15,
+                                    maxiter=200)
+            psi = piece.U(tstar) @ start
+            psi = psi / np.linalg.norm(psi)
+            self.n_jumps += 1
+            u1, u2, rnext = philox.jump_draws(self.seed, self.traj, self.n_jumps)
+            al, m, a, cls, psi = choose_jump(piece.fr, psi, u1, u2)
+            eig = piece.fr.eig
+            self.jumps.append(dict(traj=self.traj, grid=grid_index, half=half,
+                                   t=t0 + elapsed + tstar, alpha=al,
+                                   src=int(eig.manifolds[m][0]), dst=a,
+                                   omega=float(eig.E[m] - eig.E[eig.level_manifold[a]])))
+            self.r = rnext
+            elapsed += tstar
+            remaining -= tstar
+            if remaining <= 0.0:
+                self.psi = psi
+                return
+
+
+def sample(inst, traj_ids, seed=None):
+    """Run the given trajectories over the whole grid.
+
+    Returns (p_gs [len(traj_ids), K], jumps (list of dicts), final psi
+    [len(traj_ids), N] in the computational basis, normalised).
+    """
+    seed = inst.seed if seed is None else seed
+    s_grid, dt = model.grid(inst)
+    tau = 0.5 * dt
+    K = len(s_grid)
+    p = np.empty((len(traj_ids), K))
+    trajs = None
+    prev = None
+    for k, fr in enumerate(ame.frames(inst)):
+        piece = Piece(fr, tau)
+        if k == 0:
+            psi0 = fr.eig.V[:, 0]
+            trajs = [Trajectory(int(t), seed, psi0) for t in traj_ids]
+        else:
+            t_prev = (k - 1) * dt
+            for tr in trajs:
+                tr.advance(prev, tau, t_prev, k - 1, 1)
+                tr.advance(piece, tau, t_prev + tau, k, 0)
+        g0 = fr.eig.manifolds[0]
+        for i, tr in enumerate(trajs):
+            c = fr.eig.V[:, g0].T @ tr.psi
+            p[i, k] = float(np.sum(np.abs(c) ** 2) / np.vdot(tr.psi, tr.psi).real)
+        prev = piece
+    jumps = [j for tr in trajs for j in tr.jumps]
+    final = np.array([tr.psi / np.linalg.norm(tr.psi) for tr in trajs])
+    return p, jumps, final
