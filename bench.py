@@ -1,0 +1,361 @@
+"""Benchmark: trajectory-steps/s of the AME quantum-jump path on GB300.
+
+Workload (default): 8-qubit transverse-field Ising annealing, N = 256 levels
+(all kept), seeded complete-graph h, J, Ohmic bath eta g^2 = 1e-3,
+omega_c = 8 pi rad/ns, T = 12.1 mK, t_f = 10 ns, 2000-point grid, M = 10^4
+trajectories. One bench step = one full propagation of all M trajectories
+over the whole grid (aqt_run), with the FP64 tables already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torch.distributed.run; each rank runs M trajectories
+with its own seed (weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trajectory-steps/s"
+UNIT = "trajectory-steps/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tf", type=float, default=10.0)
+    ap.add_argument("--M", type=int, default=10_000)
+    ap.add_argument("--n-grid", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    ap.add_argument("--cpu-sample-traj", type=int, default=400)
+    return ap.parse_args()
+
+
+def workload(args):
+    import workloads as W
+    return W.cfg_main(t_f=args.tf, M=args.M, n_grid=args.n_grid)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks -----
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clocks_setting"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while timing."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[2], 16)
+            except ValueError:
+                continue
+            for b, name in REASON_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def alu_fp32_peak_tflops(num_sms: int, mhz: float) -> float:
+    # 128 FP32 FMA lanes per SM per clock, 2 flops per FMA
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def alu_fp64_peak_tflops(num_sms: int, mhz: float) -> float:
+    # 1.25 TFLOP/s FP64 nominal on GB300 at 2070 MHz, scaled by clock
+    return 1.25 * mhz / 2070.0
+
+
+# ------------------------------------------------------------- CPU baseline ---
+def cpu_baseline_run(args, n_traj: int, n_steps: int):
+    """The FP64 oracle's trajectory propagation on a bounded sample of the
+    workload: n_traj trajectories over the first n_steps grid steps. The
+    per-grid eigensystem/propagator setup is excluded, as the GPU's FP64
+    table build is excluded from its number. Single thread."""
+    from oracle import ame, trajectories
+    inst = workload(args)
+    _, dt = __import__("oracle.model", fromlist=["grid"]).grid(inst)
+    tau = 0.5 * dt
+    prop_time = 0.0
+    trajs = None
+    prev = None
+    for k, fr in enumerate(ame.frames(inst)):
+        if k > n_steps:
+            break
+        piece = trajectories.Piece(fr, tau)
+        if k == 0:
+            trajs = [trajectories.Trajectory(t, inst.seed, fr.eig.V[:, 0]) for t in range(n_traj)]
+        else:
+            t0 = time.perf_counter()
+            for tr in trajs:
+                tr.advance(prev, tau, (k - 1) * dt, k - 1, 1)
+                tr.advance(piece, tau, (k - 1) * dt + tau, k, 0)
+            prop_time += time.perf_counter() - t0
+        prev = piece
+    return n_traj * n_steps / prop_time, prop_time
+
+
+def cpu_baseline(args, n_traj=None, n_steps=None):
+    """Run the oracle leg in a single-threaded child process."""
+    n_traj = n_traj or args.cpu_sample_traj
+    n_steps = n_steps or args.cpu_sample_steps
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "a = bench.parse_from(%r); v, t = bench.cpu_baseline_run(a, %d, %d); "
+            "print(json.dumps({'value': v, 'seconds': t}))") % (ROOT, sys.argv[1:], n_traj, n_steps)
+    r = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                       text=True, timeout=1800)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_traj} trajectories x first {n_steps} grid steps of the same workload, FP64 "
+                      f"numpy/scipy, propagation only ({d['seconds']:.1f} s)"}
+
+
+def parse_from(argv):
+    old = sys.argv
+    sys.argv = [old[0]] + list(argv)
+    try:
+        return parse()
+    finally:
+        sys.argv = old
+
+
+# ------------------------------------------------------------------ ours ------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1710_03431_gb300 import aqt as A
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    inst = workload(args)
+    prec = A.AQT_PREC_FP32 if args.precision == "fp32" else A.AQT_PREC_FP64
+    seed = inst.seed + rank
+    sess = A.Session(inst, precision=prec, device=local, seed=seed)
+    t0 = time.perf_counter()
+    sess.build()
+    torch.cuda.synchronize()
+    table_s = time.perf_counter() - t0
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sess.run()
+    # timed region
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        A.aqt_run(sess.ctx, stream.cuda_stream)
+        b.record(stream)
+        per.append((a, b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    status = A.aqt_sync(sess.ctx)
+    ck = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kern_ms = [a.elapsed_time(b) for a, b in per]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    N, M, K = 1 << inst.n_qubits, sess.M, inst.n_grid
+    traj_steps = M * (K - 1)
+    value = world * traj_steps / (ms_per_step / 1e3)
+    mean, se = sess.observables()
+    jumps, dropped = sess.jumps()
+
+    # e2e: the public C ABI with host buffers, tables built inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        ctx2 = A.aqt_create(local)
+        ws = sess.ws
+        h2d = 0
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            A.aqt_set_ising(ctx2, inst.n_qubits, inst.hz, inst.J)
+            A.aqt_set_schedule(ctx2, inst.sched_s, inst.sched_A, inst.sched_B)
+            A.aqt_set_bath(ctx2, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
+            A.aqt_set_grid(ctx2, inst.t_f, inst.n_grid)
+            A.aqt_set_trajectories(ctx2, M, seed, prec, sess.jcap)
+            A.aqt_bind_workspace(ctx2, ws.data_ptr(), ws.numel())
+            A.aqt_build_tables(ctx2, stream.cuda_stream)
+            A.aqt_run(ctx2, stream.cuda_stream)
+            A.aqt_sync(ctx2)
+            m2, s2 = A.aqt_get_observables(ctx2, K)
+        e2e_s = (time.perf_counter() - t1) / args.e2e_steps
+        A.aqt_destroy(ctx2)
+        rs = 8 if prec == A.AQT_PREC_FP64 else 4
+        n = inst.n_qubits
+        h2d = (K * N * (2 * 8 + 2 * 8 + 2 * 4 + 8 + 8 + 4 + 4) + K * n * N * 8 + K * n * N * N * 8 + K * 16
+               + (K - 1) * N * N * rs)
+        e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(K * 2 * 8 + 12), "seconds_per_step": e2e_s,
+               "includes": "set_* + FP64 host table build + H2D + run + sync + observables D2H"}
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(local)
+    num_sms = props.multi_processor_count
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    flops = 4.0 * N * N * traj_steps
+    mhz = ck.get("sm_max_mhz") or 2070.0
+    if prec == A.AQT_PREC_FP32:
+        peak = alu_fp32_peak_tflops(num_sms, mhz)
+        peak_src = f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+    else:
+        peak = alu_fp64_peak_tflops(num_sms, mhz)
+        peak_src = f"FP64: 1.25 TFLOP/s nominal scaled to {mhz:.0f} MHz"
+    achieved = flops / kern_avg_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"propagate_simt<{'float' if prec else 'double'}>",
+            "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state)",
+            "peak_source": peak_src}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == A.AQT_PREC_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": f"tfim-{inst.n_qubits}q-N{N}-M{M}-grid{K}-tf{inst.t_f:g}ns",
+                   "N": N, "M": M, "n_grid": K, "t_f_ns": inst.t_f, "precision": args.precision,
+                   "tables": "FP64 eigensystems, rates, jump tables; rotation tables in the state precision",
+                   "l2": f"rotation tables {((K - 1) * N * N * (4 if prec else 8)) / 1e9:.2f} GB > L2, read once per step",
+                   "parallelism": f"trajectories x{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck,
+        "table_build_s": table_s, "status": A.STATUS_NAMES.get(status, status),
+        "gs_population_final": {"mean": float(mean[-1]), "stderr": float(se[-1])},
+        "jumps_per_trajectory": (len(jumps) + dropped) / M,
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------- reference ------
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state beyond imports
+    d = None
+    for _ in range(args.steps):
+        d = cpu_baseline(args, n_traj=max(8, args.cpu_sample_traj // 4), n_steps=max(5, args.cpu_sample_steps // 4))
+        if d["value"] is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle leg failed: " + d.get("error", "")[:200]}))
+            return
+        vals.append(d["value"])
+    v = statistics.mean(vals)
+    inst = workload(args)
+    N = 1 << inst.n_qubits
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"tfim-{inst.n_qubits}q-N{N}-M{inst.M}-grid{inst.n_grid}-tf{inst.t_f:g}ns",
+                   "N": N, "M": inst.M, "n_grid": inst.n_grid, "t_f_ns": inst.t_f},
+        "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": d["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

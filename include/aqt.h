@@ -1,0 +1,162 @@
+/*
+ * aqt — quantum-jump trajectories of the time-dependent adiabatic master
+ * equation (AME) on one GB300 GPU (sm_103a).
+ *
+ * Method: Yip, Albash, Lidar, "Quantum trajectories for time-dependent
+ * adiabatic master equations" (arXiv:1710.03431). The library propagates M
+ * independent N-level trajectories of a transverse-field Ising annealing
+ * Hamiltonian under the non-Hermitian effective Hamiltonian of Sec. III
+ * (Eq. Heff), detects each trajectory's jump when its squared norm falls to
+ * a uniform random threshold (Sec. IV; App. C), draws the jump channel with
+ * the probabilities of App. B.1 (Eq. Pi(t)), applies it (Eq. jump),
+ * renormalises, and accumulates the ground-state population (Sec. V) with
+ * its standard error (Sec. VI.A, Eq. stderror).
+ *
+ * Conventions (all calls):
+ *  - Units: hbar = 1; energies and rates in rad/ns, times in ns, beta in ns.
+ *  - Basis index x = sum_i bit_i 2^i; qubit i <-> bit i; bit 0 <-> sz = +1.
+ *  - Every call returns an aqt_status; errors are returned, never thrown.
+ *    After a non-OK status, aqt_last_error() gives a one-line reason.
+ *  - Host arrays passed in are copied before the call returns; the library
+ *    keeps no host pointer of the caller.
+ *  - Device memory is owned by the caller: one workspace buffer, sized by
+ *    aqt_workspace_size() and bound with aqt_bind_workspace(). The library
+ *    allocates no device memory of its own.
+ *  - Streams are the caller's (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream).
+ *  - A context is not thread-safe; use one per host thread.
+ *
+ * Call order: create -> set_ising, set_schedule, set_bath, set_grid,
+ * set_trajectories -> workspace_size -> bind_workspace -> build_tables ->
+ * run -> sync -> get_observables / get_jumps / get_final_state. Changing any
+ * set_* input invalidates the tables and the workspace size.
+ */
+#ifndef AQT_H
+#define AQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aqt_ctx aqt_ctx;
+
+typedef enum {
+    AQT_OK = 0,
+    AQT_EINVAL = 1,     /* bad argument, bad call order, or size out of range */
+    AQT_ECUDA = 2,      /* a CUDA runtime call failed (message names it) */
+    AQT_ENOMEM = 3,     /* bound workspace smaller than aqt_workspace_size() */
+    AQT_EOVERFLOW = 4,  /* jump log full: records were dropped (run completed) */
+    AQT_ENUMERIC = 5,   /* non-finite or non-positive norm, or too many jumps in one half-step */
+    AQT_ENOCONV = 6,    /* eigensolver did not converge */
+    AQT_EDEGEN = 7,     /* degenerate structure outside what the GPU path supports */
+    AQT_ENODEV = 8      /* context has no device (created with device -1) */
+} aqt_status;
+
+/* Propagation precision of the rotation step (the jump clock, jump-time root,
+ * channel draw and the tables are always FP64). */
+typedef enum {
+    AQT_PREC_FP64 = 0,      /* SIMT FP64 state and rotation */
+    AQT_PREC_FP32 = 1       /* SIMT FP32 state and rotation, FP64 norm sums */
+} aqt_precision;
+
+/* One jump. t is the jump time in ns; the jump happened while the generator
+ * was frozen at grid point `grid`, in the half-step before s_grid (half = 0)
+ * or after it (half = 1). alpha is the qubit whose sz caused it; src is the
+ * lowest level of the source degenerate manifold and dst the target level
+ * (instantaneous eigenbasis, ascending energy); omega = E(src) - E(dst) is
+ * its Bohr frequency (rad/ns). */
+typedef struct {
+    int32_t traj, grid, half, alpha, src, dst;
+    double t, omega;
+} aqt_jump;
+
+/* Create a context on CUDA device `device` (>= 0), or a host-only context
+ * (device = -1) that can build and inspect tables but not run. *out is NULL
+ * on failure. */
+aqt_status aqt_create(aqt_ctx **out, int device);
+void aqt_destroy(aqt_ctx *ctx);
+const char *aqt_last_error(const aqt_ctx *ctx);
+
+/* Ising terms of H_S (Sec. V, Eq. H_S, with the field sign written out):
+ *   H(s) = A(s) (-sum_i sx_i) + B(s) (sum_i hz_i sz_i + sum_{i<j} Jzz_ij sz_i sz_j).
+ * The paper's H^Z = -sum h sz + sum J sz sz maps to hz = -h.
+ * n_qubits in [1, 10]; hz[n]; Jzz[n*n] row-major, entries with i < j used. */
+aqt_status aqt_set_ising(aqt_ctx *ctx, int n_qubits, const double *hz, const double *Jzz);
+
+/* Piecewise-linear annealing schedule through n_knots (s, A, B) points,
+ * s strictly increasing from 0 to 1 (Sec. V, Eq. H_S; App. D). */
+aqt_status aqt_set_schedule(aqt_ctx *ctx, int n_knots, const double *s, const double *A,
+                            const double *B);
+
+/* Ohmic bath of Sec. V: gamma(w) = 2 pi eta_g2 w e^{-|w|/omega_c} / (1 - e^{-beta w}),
+ * independent sz coupling per qubit. lamb_shift = 1 adds
+ * H_LS = sum S(w) L^dag L with S(w) = (1/2pi) P int gamma(x)/(w - x) dx (Sec. II; App. E). */
+aqt_status aqt_set_bath(aqt_ctx *ctx, double eta_g2, double omega_c, double beta, int lamb_shift);
+
+/* Shared time grid s_k = k/(n_grid-1), t_k = s_k t_f, n_grid >= 2. The generator
+ * is frozen at s_{k-1} for the first half of [t_{k-1}, t_k] and at s_k for the
+ * second (symmetric split; the paper leaves the integrator open, Sec. IV). */
+aqt_status aqt_set_grid(aqt_ctx *ctx, double t_f, int n_grid);
+
+/* M trajectories, all starting in the ground state of H_S(0) (Sec. V.A).
+ * Random streams: Philox4x64-10, key (seed, 0x171003431), counter
+ * (trajectory, event, 0, 0); event 0 gives the first threshold, event j the
+ * draws of the j-th jump. jump_capacity = records kept on the device. */
+aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int precision,
+                                int64_t jump_capacity);
+
+/* Device bytes the caller must provide for the current inputs. */
+aqt_status aqt_workspace_size(aqt_ctx *ctx, size_t *bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, at least
+ * aqt_workspace_size bytes). It must stay allocated until the context is
+ * destroyed or rebound; the library never frees it. */
+aqt_status aqt_bind_workspace(aqt_ctx *ctx, void *dptr, size_t bytes);
+
+/* Build the FP64 per-grid-point tables (instantaneous eigensystems,
+ * degenerate manifolds and Bohr classes per Eq. Lindblad2, the eigenframe
+ * H_eff of Eq. Heff, rate tables, frame rotations) on the host, then copy
+ * them into the workspace on `stream`. Blocks until the copies are queued and
+ * the host buffers may be reused. Errors: AQT_ENOCONV, AQT_EDEGEN, AQT_ECUDA.
+ * On a host-only context the tables are built and kept for aqt_debug_table. */
+aqt_status aqt_build_tables(aqt_ctx *ctx, void *stream);
+
+/* Propagate all trajectories over the whole grid (Sec. IV). Asynchronous on
+ * `stream`; results are valid after aqt_sync. Each call restarts from the
+ * initial state with the same random streams. */
+aqt_status aqt_run(aqt_ctx *ctx, void *stream);
+
+/* Wait for the last run and return its device status: AQT_OK, AQT_EOVERFLOW
+ * (jump records dropped) or AQT_ENUMERIC. */
+aqt_status aqt_sync(aqt_ctx *ctx);
+
+/* Ground-manifold population at each grid point: mean[n_grid] and the
+ * standard error of the mean stderr_[n_grid] (Eq. stderror). */
+aqt_status aqt_get_observables(aqt_ctx *ctx, double *mean, double *stderr_);
+
+/* Raw FP64 sums over trajectories, sum_x[n_grid] and sum_x2[n_grid]. */
+aqt_status aqt_get_observable_sums(aqt_ctx *ctx, double *sum_x, double *sum_x2);
+
+/* Copy up to cap jump records, sorted by (traj, t), to host_buf.
+ * *n_out = records copied, *n_dropped = records lost to a full device log. */
+aqt_status aqt_get_jumps(aqt_ctx *ctx, aqt_jump *host_buf, int64_t cap, int64_t *n_out,
+                         int64_t *n_dropped);
+
+/* Final normalised states at s = 1, host_buf[M][N][2] (re, im) FP64.
+ * basis 0: instantaneous eigenbasis of H_S(1) (the library's eigenvector
+ * signs); basis 1: computational basis. */
+aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
+
+/* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
+ * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 M_alpha = V^T sz_alpha V,
+ * [n][N][N]; 4 frame rotation O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1);
+ * 5 eigenvectors V [N][N] (column a = level a); 6 manifold energy per level [N]. */
+aqt_status aqt_debug_table(aqt_ctx *ctx, int which, int grid, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AQT_H */

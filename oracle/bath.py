@@ -87,7 +87,10 @@ def _lamb_node_values(args):
 @functools.lru_cache(maxsize=16)
 def _lamb_spline(eta_g2: float, omega_c: float, beta: float, wmax: float):
     nodes = _lamb_nodes(wmax)
+    # A spawn pool only from the main process (a worker never starts another).
     workers = max(1, min(16, os.cpu_count() or 1))
+    if multiprocessing.current_process().name != "MainProcess":
+        workers = 1
     chunks = [(c, eta_g2, omega_c, beta) for c in np.array_split(nodes, 4 * workers)]
     if workers > 1:
         ctx = multiprocessing.get_context("spawn")

@@ -1,0 +1,256 @@
+"""ctypes binding of libaqt.so: the C ABI of include/aqt.h under the same names.
+
+Argument marshalling only; every computation runs in the library. The
+``Session`` helper adds what PyTorch is here for: a device workspace tensor
+and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaqt.so")
+
+AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV = range(9)
+AQT_PREC_FP64, AQT_PREC_FP32 = 0, 1
+STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4: "AQT_EOVERFLOW",
+                5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV"}
+
+EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
+           "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
+           "aqt_bind_workspace", "aqt_build_tables", "aqt_run", "aqt_sync", "aqt_get_observables",
+           "aqt_get_observable_sums", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table"]
+
+
+class aqt_jump(C.Structure):
+    _fields_ = [("traj", C.c_int32), ("grid", C.c_int32), ("half", C.c_int32), ("alpha", C.c_int32),
+                ("src", C.c_int32), ("dst", C.c_int32), ("t", C.c_double), ("omega", C.c_double)]
+
+
+JUMP_DTYPE = np.dtype([("traj", "<i4"), ("grid", "<i4"), ("half", "<i4"), ("alpha", "<i4"),
+                       ("src", "<i4"), ("dst", "<i4"), ("t", "<f8"), ("omega", "<f8")])
+
+
+class AqtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libaqt.so; raise if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, D, I, I64, U64, SZ = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int64, C.c_uint64, C.c_size_t
+        sig = {
+            "aqt_create": (I, [C.POINTER(P), I]),
+            "aqt_destroy": (None, [P]),
+            "aqt_last_error": (C.c_char_p, [P]),
+            "aqt_set_ising": (I, [P, I, D, D]),
+            "aqt_set_schedule": (I, [P, I, D, D, D]),
+            "aqt_set_bath": (I, [P, C.c_double, C.c_double, C.c_double, I]),
+            "aqt_set_grid": (I, [P, C.c_double, I]),
+            "aqt_set_trajectories": (I, [P, I64, U64, I, I64]),
+            "aqt_workspace_size": (I, [P, C.POINTER(SZ)]),
+            "aqt_bind_workspace": (I, [P, P, SZ]),
+            "aqt_build_tables": (I, [P, P]),
+            "aqt_run": (I, [P, P]),
+            "aqt_sync": (I, [P]),
+            "aqt_get_observables": (I, [P, D, D]),
+            "aqt_get_observable_sums": (I, [P, D, D]),
+            "aqt_get_jumps": (I, [P, C.POINTER(aqt_jump), I64, C.POINTER(I64), C.POINTER(I64)]),
+            "aqt_get_final_state": (I, [P, I, D]),
+            "aqt_debug_table": (I, [P, I, I, D]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _check(ctx, st):
+    if st != AQT_OK:
+        msg = lib().aqt_last_error(ctx).decode() if ctx else ""
+        raise AqtError(st, msg)
+
+
+# ---- same-name wrappers ----------------------------------------------------------
+def aqt_create(device: int = 0):
+    h = C.c_void_p()
+    st = lib().aqt_create(C.byref(h), device)
+    if st != AQT_OK:
+        raise AqtError(st, f"aqt_create(device={device})")
+    return h
+
+
+def aqt_destroy(ctx):
+    lib().aqt_destroy(ctx)
+
+
+def aqt_last_error(ctx) -> str:
+    return lib().aqt_last_error(ctx).decode()
+
+
+def aqt_set_ising(ctx, n_qubits, hz, Jzz):
+    hz, J = _f64(hz), _f64(Jzz).reshape(-1)
+    _check(ctx, lib().aqt_set_ising(ctx, int(n_qubits), _dp(hz), _dp(J)))
+
+
+def aqt_set_schedule(ctx, s, A, B):
+    s, A, B = _f64(s), _f64(A), _f64(B)
+    _check(ctx, lib().aqt_set_schedule(ctx, len(s), _dp(s), _dp(A), _dp(B)))
+
+
+def aqt_set_bath(ctx, eta_g2, omega_c, beta, lamb_shift):
+    _check(ctx, lib().aqt_set_bath(ctx, float(eta_g2), float(omega_c), float(beta), int(bool(lamb_shift))))
+
+
+def aqt_set_grid(ctx, t_f, n_grid):
+    _check(ctx, lib().aqt_set_grid(ctx, float(t_f), int(n_grid)))
+
+
+def aqt_set_trajectories(ctx, M, seed, precision, jump_capacity):
+    _check(ctx, lib().aqt_set_trajectories(ctx, int(M), int(seed) & (2**64 - 1), int(precision),
+                                           int(jump_capacity)))
+
+
+def aqt_workspace_size(ctx) -> int:
+    n = C.c_size_t()
+    _check(ctx, lib().aqt_workspace_size(ctx, C.byref(n)))
+    return n.value
+
+
+def aqt_bind_workspace(ctx, dptr: int, nbytes: int):
+    _check(ctx, lib().aqt_bind_workspace(ctx, C.c_void_p(dptr), nbytes))
+
+
+def aqt_build_tables(ctx, stream: int = 0):
+    _check(ctx, lib().aqt_build_tables(ctx, C.c_void_p(stream)))
+
+
+def aqt_run(ctx, stream: int = 0):
+    _check(ctx, lib().aqt_run(ctx, C.c_void_p(stream)))
+
+
+def aqt_sync(ctx) -> int:
+    """Returns the status (AQT_OK or AQT_EOVERFLOW); raises on other errors."""
+    st = lib().aqt_sync(ctx)
+    if st not in (AQT_OK, AQT_EOVERFLOW):
+        _check(ctx, st)
+    return st
+
+
+def aqt_get_observables(ctx, n_grid: int):
+    mean, se = np.empty(n_grid), np.empty(n_grid)
+    _check(ctx, lib().aqt_get_observables(ctx, _dp(mean), _dp(se)))
+    return mean, se
+
+
+def aqt_get_observable_sums(ctx, n_grid: int):
+    s1, s2 = np.empty(n_grid), np.empty(n_grid)
+    _check(ctx, lib().aqt_get_observable_sums(ctx, _dp(s1), _dp(s2)))
+    return s1, s2
+
+
+def aqt_get_jumps(ctx, cap: int):
+    buf = (aqt_jump * max(cap, 1))()
+    n_out, n_drop = C.c_int64(), C.c_int64()
+    _check(ctx, lib().aqt_get_jumps(ctx, buf, int(cap), C.byref(n_out), C.byref(n_drop)))
+    arr = np.frombuffer(bytes(buf), dtype=JUMP_DTYPE)[: n_out.value].copy()
+    return arr, n_drop.value
+
+
+def aqt_get_final_state(ctx, basis: int, M: int, N: int):
+    out = np.empty((M, N, 2))
+    _check(ctx, lib().aqt_get_final_state(ctx, int(basis), _dp(out)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def aqt_debug_table(ctx, which: int, grid: int, shape):
+    out = np.empty(int(np.prod(shape)))
+    _check(ctx, lib().aqt_debug_table(ctx, int(which), int(grid), _dp(out)))
+    return out.reshape(shape)
+
+
+# ---- convenience ------------------------------------------------------------------
+class Session:
+    """One context configured from an instance (see ``workloads.Instance``),
+    with its workspace held as a torch uint8 tensor on the context's device."""
+
+    def __init__(self, inst, precision=AQT_PREC_FP64, jump_capacity=None, device=0, M=None, seed=None):
+        self.inst = inst
+        self.device = device
+        self.M = int(inst.M if M is None else M)
+        self.N = 1 << inst.n_qubits
+        self.K = inst.n_grid
+        self.ctx = aqt_create(device)
+        self.jcap = int(jump_capacity if jump_capacity is not None else max(1024, 64 * self.M))
+        self.configure(inst, precision, seed)
+        self.ws = None
+
+    def configure(self, inst, precision, seed=None):
+        c = self.ctx
+        aqt_set_ising(c, inst.n_qubits, inst.hz, inst.J)
+        aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
+        aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
+        aqt_set_grid(c, inst.t_f, inst.n_grid)
+        aqt_set_trajectories(c, self.M, inst.seed if seed is None else seed, precision, self.jcap)
+
+    def allocate(self):
+        import torch
+        nbytes = aqt_workspace_size(self.ctx)
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        aqt_bind_workspace(self.ctx, self.ws.data_ptr(), self.ws.numel())
+
+    @staticmethod
+    def stream() -> int:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def build(self):
+        self.allocate()
+        aqt_build_tables(self.ctx, self.stream())
+
+    def run(self):
+        aqt_run(self.ctx, self.stream())
+        return aqt_sync(self.ctx)
+
+    def observables(self):
+        return aqt_get_observables(self.ctx, self.K)
+
+    def jumps(self):
+        return aqt_get_jumps(self.ctx, self.jcap)
+
+    def final_state(self, basis=1):
+        return aqt_get_final_state(self.ctx, basis, self.M, self.N)
+
+    def close(self):
+        if self.ctx:
+            aqt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,106 @@
+// Internal declarations shared by the host table builder, the C ABI and the
+// CUDA kernels of the AME trajectory library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/aqt.h"
+
+namespace aqt {
+
+// ---------------------------------------------------------------- bath -----
+struct Bath {
+    double eta_g2 = 0.0, omega_c = 1.0, beta = 1.0;
+    bool lamb_shift = false;
+    struct Zone {
+        double h = 0.0, half = 0.0;
+        int n0 = 0;
+        std::vector<double> val;
+    };
+    std::vector<Zone> zones;
+    double gamma(double w) const;
+    double lamb_direct(double w) const;
+    double lamb(double w) const;
+    void build_lamb(double wmax);
+};
+
+bool sym_eigen(int n, double *A, double *evals, double *V);
+
+// --------------------------------------------------------------- tables -----
+// Per-grid-point metadata (device-visible POD).
+struct GridMeta {
+    int32_t degenerate;  // some degenerate manifold has more than one level
+    int32_t gs_size;     // size of the lowest manifold (observable support)
+    double tol;          // energy tolerance for manifolds and Bohr classes
+};
+
+struct Tables {
+    int n = 0, N = 0, K = 0;
+    double dt = 0.0, tau = 0.0;
+    std::vector<double> evals;   // [K][N]
+    std::vector<double> V;       // [K][N][N]  row x, column a
+    std::vector<double> kdiag;   // [K][N][2]  diag of the eigenframe H_eff
+    std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
+    std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
+    std::vector<double> G;       // [K][n][N]  sum_a gamma(w_ab) M_alpha[a,b]^2
+    std::vector<double> M;       // [K][n][N][N] M_alpha = V^T sz_alpha V (symmetric)
+    std::vector<double> lvlE;    // [K][N]     energy of each level's manifold
+    std::vector<int32_t> mfirst; // [K][N]     first level of each level's manifold
+    std::vector<int32_t> msize;  // [K][N]     size of each level's manifold
+    std::vector<GridMeta> meta;  // [K]
+    std::vector<double> OT;      // [K-1][N][N] transpose of O_g = V_{g+1}^T V_g: OT[b][a] = O[a][b]
+};
+
+struct Inputs {
+    int n = 0;
+    std::vector<double> hz, J;
+    std::vector<double> ks, kA, kB;
+    Bath bath;
+    bool have_ising = false, have_sched = false, have_bath = false, have_grid = false, have_traj = false;
+    double t_f = 0.0;
+    int K = 0;
+    int64_t M = 0;
+    uint64_t seed = 0;
+    int precision = 0;
+    int64_t jcap = 0;
+};
+
+// Returns AQT_OK or an error with a message in *err.
+aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
+
+// ------------------------------------------------------------- kernels ------
+struct DevTables {
+    const double *kdiag, *ehalf, *d2, *G, *M, *lvlE;
+    const float *ehalf32;
+    const int32_t *mfirst, *msize;
+    const GridMeta *meta;
+    const void *OT;  // FP64 or FP32, per precision
+};
+
+struct RunParams {
+    int n, N, K, TT, RA, n_cta;
+    int64_t M;
+    uint64_t seed;
+    double tau, dt;
+    double eta_g2, omega_c, beta;
+    DevTables tab;
+    double *final_state;           // [M][N][2]
+    aqt_jump *jumps;
+    int64_t jcap;
+    unsigned long long *jcount;
+    double *obs_part;              // [n_cta][K][2]
+    double *obs_sum;               // [K][2]
+    double *scratch;               // [n_cta][8][2][N][2] FP64 jump scratch
+    int32_t *status;
+};
+
+// Launch the propagation (precision per aqt_precision) and the observable
+// reduction on `stream`. Returns a CUDA error code (0 on success).
+int launch_run(const RunParams &p, int precision, void *stream, size_t smem_bytes);
+size_t simt_smem_bytes(int N, int TT, int precision);
+void simt_shape(int N, int64_t M, int precision, int num_sms, int *TT, int *RA);
+
+}  // namespace aqt

@@ -1,0 +1,457 @@
+// C ABI of the AME trajectory library (declarations and contracts in include/aqt.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "aqt_internal.h"
+
+using namespace aqt;
+
+struct Layout {
+    size_t kdiag, ehalf, ehalf32, d2, G, M, lvlE, mfirst, msize, meta, OT;
+    size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, total;
+};
+
+struct aqt_ctx {
+    int device = -1;
+    int num_sms = 152;
+    std::string err;
+    Inputs in;
+    Tables tab;
+    bool tables_built = false;
+    bool tables_on_device = false;
+    // launch shape
+    int TT = 0, RA = 0, n_cta = 0;
+    size_t smem = 0;
+    Layout lay{};
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool ran = false;
+};
+
+namespace {
+
+aqt_status fail(aqt_ctx *c, aqt_status s, const std::string &m) {
+    if (c) c->err = m;
+    return s;
+}
+
+aqt_status cuda_fail(aqt_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, AQT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool inputs_complete(const aqt_ctx *c) {
+    const Inputs &in = c->in;
+    return in.have_ising && in.have_sched && in.have_bath && in.have_grid && in.have_traj;
+}
+
+void invalidate(aqt_ctx *c) {
+    c->tables_built = false;
+    c->tables_on_device = false;
+    c->ran = false;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void compute_layout(aqt_ctx *c) {
+    const Inputs &in = c->in;
+    const size_t n = in.n, N = (size_t)1 << in.n, K = in.K;
+    const size_t rs = in.precision == AQT_PREC_FP64 ? 8 : 4;
+    simt_shape((int)N, in.M, in.precision, c->num_sms, &c->TT, &c->RA);
+    c->n_cta = (int)((in.M + c->TT - 1) / c->TT);
+    c->smem = simt_smem_bytes((int)N, c->TT, in.precision);
+    Layout &L = c->lay;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.kdiag = take(K * N * 2 * 8);
+    L.ehalf = take(K * N * 2 * 8);
+    L.ehalf32 = take(K * N * 2 * 4);
+    L.d2 = take(K * N * 8);
+    L.G = take(K * n * N * 8);
+    L.M = take(K * n * N * N * 8);
+    L.lvlE = take(K * N * 8);
+    L.mfirst = take(K * N * 4);
+    L.msize = take(K * N * 4);
+    L.meta = take(K * sizeof(GridMeta));
+    L.OT = take((K - 1) * N * N * rs);
+    L.final_state = take((size_t)in.M * N * 2 * 8);
+    L.jumps = take((size_t)std::max<int64_t>(in.jcap, 1) * sizeof(aqt_jump));
+    L.jcount = take(8);
+    L.obs_part = take((size_t)c->n_cta * K * 2 * 8);
+    L.obs_sum = take(K * 2 * 8);
+    L.scratch = take((size_t)c->n_cta * 8 * 2 * N * 2 * 8);
+    L.status = take(4);
+    L.total = off;
+}
+
+aqt_status use_device(aqt_ctx *c) {
+    if (c->device < 0) return fail(c, AQT_ENODEV, "context was created without a device");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return AQT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+aqt_status aqt_create(aqt_ctx **out, int device) {
+    if (!out) return AQT_EINVAL;
+    *out = nullptr;
+    aqt_ctx *c = new (std::nothrow) aqt_ctx();
+    if (!c) return AQT_EINVAL;
+    c->device = device;
+    if (device >= 0) {
+        int nd = 0;
+        cudaError_t e = cudaGetDeviceCount(&nd);
+        if (e != cudaSuccess || device >= nd) {
+            delete c;
+            return AQT_ECUDA;
+        }
+        e = cudaSetDevice(device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) {
+            delete c;
+            return AQT_ECUDA;
+        }
+    } else if (device != -1) {
+        delete c;
+        return AQT_EINVAL;
+    }
+    *out = c;
+    return AQT_OK;
+}
+
+void aqt_destroy(aqt_ctx *c) { delete c; }
+
+const char *aqt_last_error(const aqt_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+aqt_status aqt_set_ising(aqt_ctx *c, int n_qubits, const double *hz, const double *Jzz) {
+    if (!c) return AQT_EINVAL;
+    if (n_qubits < 1 || n_qubits > 10) return fail(c, AQT_EINVAL, "n_qubits must be in [1, 10]");
+    if (!hz || !Jzz) return fail(c, AQT_EINVAL, "hz and Jzz must be non-null");
+    for (int i = 0; i < n_qubits; ++i)
+        if (!std::isfinite(hz[i])) return fail(c, AQT_EINVAL, "hz has a non-finite entry");
+    for (int i = 0; i < n_qubits * n_qubits; ++i)
+        if (!std::isfinite(Jzz[i])) return fail(c, AQT_EINVAL, "Jzz has a non-finite entry");
+    c->in.n = n_qubits;
+    c->in.hz.assign(hz, hz + n_qubits);
+    c->in.J.assign(Jzz, Jzz + n_qubits * n_qubits);
+    c->in.have_ising = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_set_schedule(aqt_ctx *c, int n_knots, const double *s, const double *A, const double *B) {
+    if (!c) return AQT_EINVAL;
+    if (n_knots < 2 || !s || !A || !B) return fail(c, AQT_EINVAL, "schedule needs >= 2 knots");
+    if (s[0] != 0.0 || s[n_knots - 1] != 1.0) return fail(c, AQT_EINVAL, "schedule knots must span [0, 1]");
+    for (int i = 0; i < n_knots; ++i) {
+        if (!std::isfinite(A[i]) || !std::isfinite(B[i])) return fail(c, AQT_EINVAL, "schedule has a non-finite value");
+        if (i && !(s[i] > s[i - 1])) return fail(c, AQT_EINVAL, "schedule knots must increase strictly");
+    }
+    c->in.ks.assign(s, s + n_knots);
+    c->in.kA.assign(A, A + n_knots);
+    c->in.kB.assign(B, B + n_knots);
+    c->in.have_sched = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_set_bath(aqt_ctx *c, double eta_g2, double omega_c, double beta, int lamb_shift) {
+    if (!c) return AQT_EINVAL;
+    if (!(eta_g2 >= 0.0) || !(omega_c > 0.0) || !(beta > 0.0) || !std::isfinite(eta_g2) ||
+        !std::isfinite(omega_c) || !std::isfinite(beta))
+        return fail(c, AQT_EINVAL, "bath needs eta_g2 >= 0, omega_c > 0, beta > 0");
+    c->in.bath = Bath();
+    c->in.bath.eta_g2 = eta_g2;
+    c->in.bath.omega_c = omega_c;
+    c->in.bath.beta = beta;
+    c->in.bath.lamb_shift = lamb_shift != 0;
+    c->in.have_bath = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_set_grid(aqt_ctx *c, double t_f, int n_grid) {
+    if (!c) return AQT_EINVAL;
+    if (!(t_f > 0.0) || !std::isfinite(t_f) || n_grid < 2 || n_grid > 1000000)
+        return fail(c, AQT_EINVAL, "grid needs t_f > 0 and 2 <= n_grid <= 1e6");
+    c->in.t_f = t_f;
+    c->in.K = n_grid;
+    c->in.have_grid = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precision, int64_t jump_capacity) {
+    if (!c) return AQT_EINVAL;
+    if (M < 1 || M > (int64_t)1 << 31) return fail(c, AQT_EINVAL, "M must be in [1, 2^31]");
+    if (precision != AQT_PREC_FP64 && precision != AQT_PREC_FP32)
+        return fail(c, AQT_EINVAL, "unknown precision");
+    if (jump_capacity < 0) return fail(c, AQT_EINVAL, "jump_capacity must be >= 0");
+    c->in.M = M;
+    c->in.seed = seed;
+    c->in.precision = precision;
+    c->in.jcap = jump_capacity;
+    c->in.have_traj = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return AQT_EINVAL;
+    if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set ising, schedule, bath, grid and trajectories first");
+    compute_layout(c);
+    *bytes = c->lay.total;
+    return AQT_OK;
+}
+
+aqt_status aqt_bind_workspace(aqt_ctx *c, void *dptr, size_t bytes) {
+    if (!c) return AQT_EINVAL;
+    if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs before binding a workspace");
+    compute_layout(c);
+    if (!dptr || ((uintptr_t)dptr & 255)) return fail(c, AQT_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < c->lay.total) return fail(c, AQT_ENOMEM, "workspace smaller than aqt_workspace_size");
+    c->ws = (unsigned char *)dptr;
+    c->ws_bytes = bytes;
+    c->tables_on_device = false;
+    c->ran = false;
+    return AQT_OK;
+}
+
+aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
+    if (!c) return AQT_EINVAL;
+    if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs before building tables");
+    if (!c->tables_built) {
+        std::string err;
+        aqt_status s = build_tables(c->in, c->tab, &err);
+        if (s != AQT_OK) return fail(c, s, err);
+        c->tables_built = true;
+    }
+    if (c->device < 0) return AQT_OK;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ws) return fail(c, AQT_EINVAL, "bind a workspace before building tables on a device");
+    compute_layout(c);
+    if (c->ws_bytes < c->lay.total) return fail(c, AQT_ENOMEM, "workspace smaller than aqt_workspace_size");
+    cudaStream_t st = (cudaStream_t)stream;
+    const Tables &t = c->tab;
+    const Layout &L = c->lay;
+    std::vector<float> e32(t.ehalf.begin(), t.ehalf.end());
+    auto put = [&](size_t off, const void *src, size_t bytes) -> cudaError_t {
+        if (!bytes) return cudaSuccess;
+        return cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    cudaError_t e = cudaSuccess;
+    if (!e) e = put(L.kdiag, t.kdiag.data(), t.kdiag.size() * 8);
+    if (!e) e = put(L.ehalf, t.ehalf.data(), t.ehalf.size() * 8);
+    if (!e) e = put(L.ehalf32, e32.data(), e32.size() * 4);
+    if (!e) e = put(L.d2, t.d2.data(), t.d2.size() * 8);
+    if (!e) e = put(L.G, t.G.data(), t.G.size() * 8);
+    if (!e) e = put(L.M, t.M.data(), t.M.size() * 8);
+    if (!e) e = put(L.lvlE, t.lvlE.data(), t.lvlE.size() * 8);
+    if (!e) e = put(L.mfirst, t.mfirst.data(), t.mfirst.size() * 4);
+    if (!e) e = put(L.msize, t.msize.data(), t.msize.size() * 4);
+    if (!e) e = put(L.meta, t.meta.data(), t.meta.size() * sizeof(GridMeta));
+    if (c->in.precision == AQT_PREC_FP64) {
+        if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
+        if (!e) e = cudaStreamSynchronize(st);
+    } else {
+        std::vector<float> o32(t.OT.begin(), t.OT.end());
+        if (!e) e = put(L.OT, o32.data(), o32.size() * 4);
+        if (!e) e = cudaStreamSynchronize(st);  // host staging buffers go out of scope
+    }
+    if (e) return cuda_fail(c, e, "table upload");
+    c->tables_on_device = true;
+    return AQT_OK;
+}
+
+aqt_status aqt_run(aqt_ctx *c, void *stream) {
+    if (!c) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->tables_on_device) return fail(c, AQT_EINVAL, "build tables on the device before running");
+    const Layout &L = c->lay;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(c->ws + L.jcount, 0, 8, st);
+    if (!e) e = cudaMemsetAsync(c->ws + L.status, 0, 4, st);
+    if (e) return cuda_fail(c, e, "cudaMemsetAsync");
+    RunParams p{};
+    const Inputs &in = c->in;
+    p.n = in.n;
+    p.N = 1 << in.n;
+    p.K = in.K;
+    p.TT = c->TT;
+    p.RA = c->RA;
+    p.n_cta = c->n_cta;
+    p.M = in.M;
+    p.seed = in.seed;
+    p.tau = c->tab.tau;
+    p.dt = c->tab.dt;
+    p.eta_g2 = in.bath.eta_g2;
+    p.omega_c = in.bath.omega_c;
+    p.beta = in.bath.beta;
+    p.tab.kdiag = (const double *)(c->ws + L.kdiag);
+    p.tab.ehalf = (const double *)(c->ws + L.ehalf);
+    p.tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
+    p.tab.d2 = (const double *)(c->ws + L.d2);
+    p.tab.G = (const double *)(c->ws + L.G);
+    p.tab.M = (const double *)(c->ws + L.M);
+    p.tab.lvlE = (const double *)(c->ws + L.lvlE);
+    p.tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
+    p.tab.msize = (const int32_t *)(c->ws + L.msize);
+    p.tab.meta = (const GridMeta *)(c->ws + L.meta);
+    p.tab.OT = c->ws + L.OT;
+    p.final_state = (double *)(c->ws + L.final_state);
+    p.jumps = (aqt_jump *)(c->ws + L.jumps);
+    p.jcap = in.jcap;
+    p.jcount = (unsigned long long *)(c->ws + L.jcount);
+    p.obs_part = (double *)(c->ws + L.obs_part);
+    p.obs_sum = (double *)(c->ws + L.obs_sum);
+    p.scratch = (double *)(c->ws + L.scratch);
+    p.status = (int32_t *)(c->ws + L.status);
+    int ce = launch_run(p, in.precision, stream, c->smem);
+    if (ce) return cuda_fail(c, (cudaError_t)ce, "kernel launch");
+    c->stream = st;
+    c->ran = true;
+    return AQT_OK;
+}
+
+aqt_status aqt_sync(aqt_ctx *c) {
+    if (!c) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "no run to wait for");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "run");
+    int32_t status = 0;
+    unsigned long long cnt = 0;
+    e = cudaMemcpy(&status, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(&cnt, c->ws + c->lay.jcount, 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "status readback");
+    if (status & 2) return fail(c, AQT_ENUMERIC, "non-finite norm or too many jumps in one half-step");
+    if ((int64_t)cnt > c->in.jcap)
+        return fail(c, AQT_EOVERFLOW, "jump log full: " + std::to_string((int64_t)cnt - c->in.jcap) + " dropped");
+    return AQT_OK;
+}
+
+aqt_status aqt_get_observable_sums(aqt_ctx *c, double *sum_x, double *sum_x2) {
+    if (!c || !sum_x || !sum_x2) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "run first");
+    const int K = c->in.K;
+    std::vector<double> buf((size_t)K * 2);
+    cudaError_t e = cudaMemcpy(buf.data(), c->ws + c->lay.obs_sum, buf.size() * 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "observable readback");
+    for (int g = 0; g < K; ++g) {
+        sum_x[g] = buf[2 * g];
+        sum_x2[g] = buf[2 * g + 1];
+    }
+    return AQT_OK;
+}
+
+aqt_status aqt_get_observables(aqt_ctx *c, double *mean, double *stderr_) {
+    if (!c || !mean || !stderr_) return AQT_EINVAL;
+    const int K = c->in.K;
+    std::vector<double> s1(K), s2(K);
+    aqt_status s = aqt_get_observable_sums(c, s1.data(), s2.data());
+    if (s != AQT_OK) return s;
+    const double R = (double)c->in.M;
+    for (int g = 0; g < K; ++g) {
+        mean[g] = s1[g] / R;
+        // Eq. stderror: sigma^2 = sum (x - mean)^2 / (R (R - 1))
+        const double ss = std::max(0.0, s2[g] - R * mean[g] * mean[g]);
+        stderr_[g] = R > 1 ? std::sqrt(ss / (R * (R - 1.0))) : 0.0;
+    }
+    return AQT_OK;
+}
+
+aqt_status aqt_get_jumps(aqt_ctx *c, aqt_jump *host_buf, int64_t cap, int64_t *n_out, int64_t *n_dropped) {
+    if (!c || !n_out || !n_dropped || cap < 0 || (cap > 0 && !host_buf)) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "run first");
+    unsigned long long cnt = 0;
+    cudaError_t e = cudaMemcpy(&cnt, c->ws + c->lay.jcount, 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "jump count readback");
+    const int64_t kept = std::min<int64_t>((int64_t)cnt, c->in.jcap);
+    std::vector<aqt_jump> all((size_t)kept);
+    if (kept) {
+        e = cudaMemcpy(all.data(), c->ws + c->lay.jumps, (size_t)kept * sizeof(aqt_jump), cudaMemcpyDeviceToHost);
+        if (e) return cuda_fail(c, e, "jump readback");
+    }
+    std::sort(all.begin(), all.end(), [](const aqt_jump &a, const aqt_jump &b) {
+        if (a.traj != b.traj) return a.traj < b.traj;
+        return a.t < b.t;
+    });
+    const int64_t nout = std::min<int64_t>(kept, cap);
+    if (nout) std::memcpy(host_buf, all.data(), (size_t)nout * sizeof(aqt_jump));
+    *n_out = nout;
+    *n_dropped = (int64_t)cnt - kept;
+    return AQT_OK;
+}
+
+aqt_status aqt_get_final_state(aqt_ctx *c, int basis, double *host_buf) {
+    if (!c || !host_buf || (basis != 0 && basis != 1)) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "run first");
+    const size_t N = (size_t)1 << c->in.n, M = (size_t)c->in.M;
+    cudaError_t e = cudaMemcpy(host_buf, c->ws + c->lay.final_state, M * N * 2 * 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "final state readback");
+    if (basis == 1) {
+        const double *V = &c->tab.V[(size_t)(c->in.K - 1) * N * N];
+        std::vector<double> tmp(N * 2);
+        for (size_t m = 0; m < M; ++m) {
+            double *cm = host_buf + m * N * 2;
+            for (size_t x = 0; x < N; ++x) {
+                double re = 0.0, im = 0.0;
+                for (size_t a = 0; a < N; ++a) {
+                    re += V[x * N + a] * cm[2 * a];
+                    im += V[x * N + a] * cm[2 * a + 1];
+                }
+                tmp[2 * x] = re;
+                tmp[2 * x + 1] = im;
+            }
+            std::memcpy(cm, tmp.data(), N * 2 * 8);
+        }
+    }
+    return AQT_OK;
+}
+
+aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
+    if (!c || !out) return AQT_EINVAL;
+    if (!c->tables_built) return fail(c, AQT_EINVAL, "build tables first");
+    const Tables &t = c->tab;
+    const size_t N = t.N, n = t.n, NN = N * N;
+    if (grid < 0 || grid >= t.K || (which == 4 && grid >= t.K - 1)) return fail(c, AQT_EINVAL, "grid out of range");
+    const size_t g = grid;
+    switch (which) {
+        case 0: std::copy_n(&t.evals[g * N], N, out); break;
+        case 1: std::copy_n(&t.kdiag[g * N * 2], N * 2, out); break;
+        case 2: std::copy_n(&t.G[g * n * N], n * N, out); break;
+        case 3: std::copy_n(&t.M[g * n * NN], n * NN, out); break;
+        case 4:
+            for (size_t a = 0; a < N; ++a)
+                for (size_t b = 0; b < N; ++b) out[a * N + b] = t.OT[g * NN + b * N + a];
+            break;
+        case 5: std::copy_n(&t.V[g * NN], NN, out); break;
+        case 6: std::copy_n(&t.lvlE[g * N], N, out); break;
+        default: return fail(c, AQT_EINVAL, "unknown table");
+    }
+    return AQT_OK;
+}
+
+}  // extern "C"

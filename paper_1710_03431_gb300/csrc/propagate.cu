@@ -1,0 +1,638 @@
+// SIMT propagation of AME quantum-jump trajectories (FP64 or FP32 state).
+//
+// arXiv:1710.03431, Sec. IV: each trajectory carries its normalised
+// eigenframe coefficients c (psi = V_g c), the log of the unnormalised
+// squared norm accumulated since its last jump (ell) and the log of its
+// threshold r. Per grid step g-1 -> g:
+//   c <- O_{g-1} c                      frame change, O = V_g^T V_{g-1} (rotation GEMM)
+//   half-step frozen at s_g:            c_a <- c_a exp(-i K_aa tau), ell += log ||c||^2
+//   observe the ground-manifold population at s_g
+//   half-step frozen at s_g (first half of the next interval)
+// with K the diagonal eigenframe H_eff (Sec. III, Eq. Heff). When ell falls to
+// log r inside a half-step (Sec. IV; App. C), the warp that owns the
+// trajectory finds the crossing time in FP64, draws the jump (App. B.1,
+// Eq. Pi(t)), applies it (Eq. jump), draws a new threshold and finishes the
+// half-step, possibly jumping again.
+//
+// Layout: one CTA owns TT trajectories for the whole run; their states stay in
+// shared memory as planar real/imaginary [level][trajectory] tiles. The frame
+// rotation streams O^T from the tables in chunks of KB rows. Each warp owns
+// whole trajectories in the per-step epilogue (norms by warp shuffles).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "aqt_internal.h"
+#include "philox.cuh"
+
+namespace aqt {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxJumpsPerHalf = 64;
+constexpr int kChunkBytes = 32768;
+
+enum : int32_t { kStatusNumeric = 2 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_incl_scan(double v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double gamma_ohmic(double w, double eta_g2, double omega_c, double beta) {
+    if (w == 0.0) return 2.0 * M_PI * eta_g2 / beta;
+    return 2.0 * M_PI * eta_g2 * w * exp(-fabs(w) / omega_c) / (-expm1(-beta * w));
+}
+
+struct Scalars {
+    double *logr, *ell;
+    int *nj;
+};
+
+// Find the first index in [0, N) chosen by inverse CDF over weights wfun(i):
+// the first i with prefix_sum(i) > target. Returns -1 if none (rounding).
+template <class WF>
+__device__ int warp_pick(int N, double target, int lane, WF wfun) {
+    double cum = 0.0;
+    int last_pos = -1;
+    for (int base = 0; base < N; base += 32) {
+        const int i = base + lane;
+        const double w = i < N ? wfun(i) : 0.0;
+        const double pre = warp_incl_scan(w, lane);
+        const double tot = __shfl_sync(0xffffffffu, pre, 31);
+        const unsigned pos = __ballot_sync(0xffffffffu, w > 0.0);
+        if (pos) last_pos = base + 31 - __clz(pos);
+        if (cum + tot > target) {
+            const unsigned hit = __ballot_sync(0xffffffffu, i < N && cum + pre > target);
+            if (hit) return base + __ffs(hit) - 1;
+        }
+        cum += tot;
+    }
+    return last_pos;
+}
+
+// Resolve every jump of one trajectory inside one frozen half-step, in FP64.
+// c64 holds the normalised state at the start of the half-step; on return it
+// holds the normalised state at its end, and ell/logr/nj are updated.
+__device__ void resolve_half(const RunParams &p, int g, int half, int64_t traj, double2 *c64, double2 *y64,
+                             double &ell, double &logr, int &nj, int lane) {
+    const int N = p.N, n = p.n;
+    const double *kd = p.tab.kdiag + (size_t)g * N * 2;
+    const double *lvlE = p.tab.lvlE + (size_t)g * N;
+    const int32_t *mfirst = p.tab.mfirst + (size_t)g * N;
+    const int32_t *msize = p.tab.msize + (size_t)g * N;
+    const GridMeta meta = p.tab.meta[g];
+    const double *Mg = p.tab.M + (size_t)g * n * N * N;
+    const double *Gg = p.tab.G + (size_t)g * n * N;
+    const double t_half0 = half == 0 ? g * p.dt - p.tau : g * p.dt;
+    double ell0 = ell, tau_rem = p.tau;
+
+    for (int it = 0;; ++it) {
+        if (it >= kMaxJumpsPerHalf) {
+            if (lane == 0) atomicOr(p.status, kStatusNumeric);
+            break;
+        }
+        // --- crossing time: root of ell0 + log sum |c|^2 e^{2 Im K t} = log r ---
+        double t = 0.0;
+        for (int k = 0; k < 200; ++k) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int a = lane; a < N; a += 32) {
+                const double im = kd[2 * a + 1];
+                const double q = (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * exp(2.0 * im * t);
+                s0 += q;
+                s1 += 2.0 * im * q;
+            }
+            s0 = warp_sum(s0);
+            s1 = warp_sum(s1);
+            const double F = ell0 + log(s0) - logr;
+            if (F <= 0.0 || s1 >= 0.0) break;
+            double tn = t - F * s0 / s1;
+            if (tn >= tau_rem) tn = tau_rem;
+            const bool done = tn - t <= 1e-16 * p.tau;
+            t = tn;
+            if (done) break;
+        }
+        // --- propagate to the crossing and renormalise -----------------------
+        {
+            double s = 0.0;
+            for (int a = lane; a < N; a += 32) {
+                const double re = kd[2 * a], im = kd[2 * a + 1];
+                double sn, cs;
+                sincos(re * t, &sn, &cs);
+                const double amp = exp(im * t);
+                const double2 v = c64[a];
+                const double2 r = make_double2(amp * (v.x * cs + v.y * sn), amp * (v.y * cs - v.x * sn));
+                c64[a] = r;
+                s += r.x * r.x + r.y * r.y;
+            }
+            s = warp_sum(s);
+            const double inv = 1.0 / sqrt(s);
+            for (int a = lane; a < N; a += 32) {
+                c64[a].x *= inv;
+                c64[a].y *= inv;
+            }
+            __syncwarp();
+        }
+        // --- draw the jump ----------------------------------------------------
+        ++nj;
+        const Philox4 rnd = traj_event(p.seed, traj, nj);
+        const double u1 = uniform01(rnd.x[0]), u2 = uniform01(rnd.x[1]), u3 = uniform01(rnd.x[2]);
+        // stage-one weight of unit (alpha, manifold starting at b)
+        auto unit_w = [&](int al, int b) -> double {
+            if (mfirst[b] != b) return 0.0;
+            const int ms = msize[b];
+            if (ms == 1) {
+                const double2 v = c64[b];
+                return (v.x * v.x + v.y * v.y) * Gg[(size_t)al * N + b];
+            }
+            return -1.0;  // computed by the warp below
+        };
+        // manifold weight for non-singleton source manifolds (degenerate grids)
+        auto manifold_w = [&](int al, int b) -> double {
+            const int ms = msize[b];
+            const double *Ma = Mg + (size_t)al * N * N;
+            double acc = 0.0;
+            for (int a = lane; a < N; a += 32) {
+                double yr = 0.0, yi = 0.0;
+                for (int bp = b; bp < b + ms; ++bp) {
+                    const double m = Ma[(size_t)a * N + bp];
+                    yr += m * c64[bp].x;
+                    yi += m * c64[bp].y;
+                }
+                acc += gamma_ohmic(lvlE[b] - lvlE[a], p.eta_g2, p.omega_c, p.beta) * (yr * yr + yi * yi);
+            }
+            return warp_sum(acc);
+        };
+        // per-alpha totals (identical on all lanes)
+        double S[16];
+        double total = 0.0;
+        for (int al = 0; al < n; ++al) {
+            double acc = 0.0;
+            for (int b = lane; b < N; b += 32) {
+                const double w = unit_w(al, b);
+                if (w > 0.0) acc += w;
+            }
+            acc = warp_sum(acc);
+            if (meta.degenerate) {
+                for (int b = 0; b < N; ++b)
+                    if (mfirst[b] == b && msize[b] > 1) acc += manifold_w(al, b);
+            }
+            S[al] = acc;
+            total += acc;
+        }
+        int al_s = -1;
+        double cum = 0.0;
+        const double target = u1 * total;
+        for (int al = 0; al < n; ++al) {
+            if (S[al] > 0.0 && cum + S[al] > target) {
+                al_s = al;
+                break;
+            }
+            cum += S[al];
+        }
+        if (al_s < 0)
+            for (int al = n - 1; al >= 0; --al)
+                if (S[al] > 0.0) {
+                    al_s = al;
+                    cum = 0.0;
+                    for (int q = 0; q < al; ++q) cum += S[q];
+                    break;
+                }
+        if (al_s < 0) {  // no channel has weight: cannot happen for a decaying norm
+            if (lane == 0) atomicOr(p.status, kStatusNumeric);
+            break;
+        }
+        int bsrc;
+        if (!meta.degenerate) {
+            bsrc = warp_pick(N, target - cum, lane, [&](int b) { return unit_w(al_s, b); });
+        } else {
+            // sequential walk over manifolds (rare path)
+            double c2 = cum;
+            bsrc = -1;
+            int lastb = -1;
+            for (int b = 0; b < N; ++b) {
+                if (mfirst[b] != b) continue;
+                const double w = msize[b] == 1 ? unit_w(al_s, b) : manifold_w(al_s, b);
+                if (w > 0.0) lastb = b;
+                if (w > 0.0 && c2 + w > target) {
+                    bsrc = b;
+                    break;
+                }
+                c2 += w;
+            }
+            if (bsrc < 0) bsrc = lastb;
+        }
+        if (bsrc < 0) {
+            if (lane == 0) atomicOr(p.status, kStatusNumeric);
+            break;
+        }
+        // stage two: target level a
+        const int ms = msize[bsrc];
+        const double *Ma = Mg + (size_t)al_s * N * N;
+        auto target_w = [&](int a) -> double {
+            const double gm = gamma_ohmic(lvlE[bsrc] - lvlE[a], p.eta_g2, p.omega_c, p.beta);
+            if (ms == 1) {
+                const double m = Ma[(size_t)a * N + bsrc];
+                return gm * m * m;
+            }
+            double yr = 0.0, yi = 0.0;
+            for (int bp = bsrc; bp < bsrc + ms; ++bp) {
+                const double m = Ma[(size_t)a * N + bp];
+                yr += m * c64[bp].x;
+                yi += m * c64[bp].y;
+            }
+            return gm * (yr * yr + yi * yi);
+        };
+        double tot2 = 0.0;
+        for (int a = lane; a < N; a += 32) tot2 += target_w(a);
+        tot2 = warp_sum(tot2);
+        const int adst = warp_pick(N, u2 * tot2, lane, target_w);
+        if (adst < 0) {
+            if (lane == 0) atomicOr(p.status, kStatusNumeric);
+            break;
+        }
+        // --- apply the class operator A_{alpha, omega*} (Eq. jump) ---------------
+        const double wstar = lvlE[bsrc] - lvlE[adst];
+        const double tol = meta.tol;
+        double s = 0.0;
+        for (int a = lane; a < N; a += 32) {
+            const double lo_e = lvlE[a] + wstar - tol, hi_e = lvlE[a] + wstar + tol;
+            int lo = 0, hi = N;  // first index with lvlE >= lo_e
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (lvlE[mid] < lo_e) lo = mid + 1; else hi = mid;
+            }
+            double yr = 0.0, yi = 0.0;
+            for (int bp = lo; bp < N && lvlE[bp] <= hi_e; ++bp) {
+                const double amp =
+                    sqrt(gamma_ohmic(lvlE[bp] - lvlE[a], p.eta_g2, p.omega_c, p.beta)) * Ma[(size_t)a * N + bp];
+                yr += amp * c64[bp].x;
+                yi += amp * c64[bp].y;
+            }
+            y64[a] = make_double2(yr, yi);
+            s += yr * yr + yi * yi;
+        }
+        s = warp_sum(s);
+        __syncwarp();
+        const double inv = 1.0 / sqrt(s);
+        for (int a = lane; a < N; a += 32) c64[a] = make_double2(y64[a].x * inv, y64[a].y * inv);
+        __syncwarp();
+        const double t_jump = t_half0 + (p.tau - tau_rem) + t;
+        if (lane == 0) {
+            const unsigned long long idx = atomicAdd(p.jcount, 1ull);
+            if ((int64_t)idx < p.jcap) {
+                aqt_jump rec;
+                rec.traj = (int32_t)traj;
+                rec.grid = g;
+                rec.half = half;
+                rec.alpha = al_s;
+                rec.src = bsrc;
+                rec.dst = adst;
+                rec.t = t_jump;
+                rec.omega = wstar;
+                p.jumps[idx] = rec;
+            }
+        }
+        logr = log(u3);
+        ell0 = 0.0;
+        tau_rem -= t;
+        // --- rest of the half-step: another crossing? ------------------------------
+        double s0 = 0.0;
+        for (int a = lane; a < N; a += 32)
+            s0 += (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * exp(2.0 * kd[2 * a + 1] * tau_rem);
+        s0 = warp_sum(s0);
+        if (tau_rem > 0.0 && log(s0) - logr <= 0.0) continue;
+        break;
+    }
+    // finish the half-step without further jumps
+    double s0 = 0.0;
+    for (int a = lane; a < N; a += 32) {
+        const double re = kd[2 * a], im = kd[2 * a + 1];
+        double sn, cs;
+        sincos(re * tau_rem, &sn, &cs);
+        const double amp = exp(im * tau_rem);
+        const double2 v = c64[a];
+        const double2 r = make_double2(amp * (v.x * cs + v.y * sn), amp * (v.y * cs - v.x * sn));
+        c64[a] = r;
+        s0 += r.x * r.x + r.y * r.y;
+    }
+    s0 = warp_sum(s0);
+    ell = ell0 + log(s0);
+    const double inv = 1.0 / sqrt(s0);
+    for (int a = lane; a < N; a += 32) {
+        c64[a].x *= inv;
+        c64[a].y *= inv;
+    }
+    __syncwarp();
+}
+
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float *p, float v[4]) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double *p, double v[4]) {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p);
+        const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ const R *ehalf_table(const RunParams &p);
+template <>
+__device__ __forceinline__ const float *ehalf_table<float>(const RunParams &p) { return p.tab.ehalf32; }
+template <>
+__device__ __forceinline__ const double *ehalf_table<double>(const RunParams &p) { return p.tab.ehalf; }
+
+// One trajectory's renormalisation, frozen half-step and crossing check.
+template <typename R>
+__device__ void half_step(const RunParams &p, int g, int half, int t, int64_t traj, R *cre, R *cim, int LD,
+                          const R *eh, const double *d2s, Scalars sc, double2 *c64, double2 *y64, int lane) {
+    const int N = p.N;
+    double nu = 0.0, f = 0.0;
+    for (int a = lane; a < N; a += 32) {
+        const double re = cre[a * LD + t], im = cim[a * LD + t];
+        const double q = re * re + im * im;
+        nu += q;
+        f += q * d2s[a];
+    }
+    nu = warp_sum(nu);
+    f = warp_sum(f);
+    if (!(nu > 0.0) || !isfinite(nu)) {
+        if (lane == 0) atomicOr(p.status, kStatusNumeric);
+        return;
+    }
+    f /= nu;
+    const double ell = sc.ell[t], logr = sc.logr[t];
+    const double ell_new = ell + log(f);
+    if (ell_new > logr) {
+        const R scale = (R)(1.0 / sqrt(f * nu));
+        for (int a = lane; a < N; a += 32) {
+            const R re = cre[a * LD + t], im = cim[a * LD + t];
+            const R er = eh[2 * a], ei = eh[2 * a + 1];
+            cre[a * LD + t] = (re * er - im * ei) * scale;
+            cim[a * LD + t] = (re * ei + im * er) * scale;
+        }
+        if (lane == 0) sc.ell[t] = ell_new;
+        __syncwarp();
+        return;
+    }
+    // crossing inside this half-step: FP64 jump resolution
+    const double inv = 1.0 / sqrt(nu);
+    for (int a = lane; a < N; a += 32)
+        c64[a] = make_double2((double)cre[a * LD + t] * inv, (double)cim[a * LD + t] * inv);
+    __syncwarp();
+    double e = ell, lr = logr;
+    int nj = sc.nj[t];
+    resolve_half(p, g, half, traj, c64, y64, e, lr, nj, lane);
+    for (int a = lane; a < N; a += 32) {
+        cre[a * LD + t] = (R)c64[a].x;
+        cim[a * LD + t] = (R)c64[a].y;
+    }
+    if (lane == 0) {
+        sc.ell[t] = e;
+        sc.logr[t] = lr;
+        sc.nj[t] = nj;
+    }
+    __syncwarp();
+}
+
+template <typename R, int RA>
+__global__ void __launch_bounds__(kThreads) propagate_simt(RunParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = p.N, K = p.K, TT = p.TT;
+    const int LD = TT + 4;
+    const int TXN = TT / 4, TYN = kThreads / TXN;
+    const int KB = min(N, max(1, kChunkBytes / (int)(N * sizeof(R))));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // shared-memory carve (all offsets multiples of 16 bytes)
+    double *d2s = reinterpret_cast<double *>(smem);
+    double *logr = d2s + N;
+    double *ell = logr + TT;
+    double *obs = ell + TT;                         // [kWarps][2]
+    int *nj = reinterpret_cast<int *>(obs + 2 * kWarps);
+    R *cre = reinterpret_cast<R *>(nj + ((TT + 3) & ~3));
+    R *cim = cre + (size_t)N * LD;
+    R *osm = cim + (size_t)N * LD;
+    R *eh = osm + (size_t)KB * N;
+    Scalars sc{logr, ell, nj};
+
+    const int64_t t0 = (int64_t)blockIdx.x * TT;
+    double2 *c64 = reinterpret_cast<double2 *>(p.scratch) + ((size_t)blockIdx.x * kWarps + warp) * 2 * N;
+    double2 *y64 = c64 + N;
+
+    // initial state: ground state of H_S(0) (level 0), threshold from event 0
+    for (int i = tid; i < N * LD; i += kThreads) {
+        const int a = i / LD, t = i % LD;
+        cre[i] = (a == 0 && t < TT && t0 + t < p.M) ? (R)1 : (R)0;
+        cim[i] = (R)0;
+    }
+    for (int t = tid; t < TT; t += kThreads) {
+        ell[t] = 0.0;
+        nj[t] = 0;
+        logr[t] = (t0 + t < p.M) ? log(uniform01(traj_event(p.seed, t0 + t, 0).x[0])) : 0.0;
+    }
+    const R *eh_tab = ehalf_table<R>(p);
+    auto load_grid = [&](int g) {
+        for (int a = tid; a < N; a += kThreads) {
+            d2s[a] = p.tab.d2[(size_t)g * N + a];
+            eh[2 * a] = eh_tab[((size_t)g * N + a) * 2];
+            eh[2 * a + 1] = eh_tab[((size_t)g * N + a) * 2 + 1];
+        }
+    };
+    const int gs0 = p.tab.meta[0].gs_size;
+    auto observe = [&](int g, int gs) {
+        double wx = 0.0, wx2 = 0.0;
+        for (int t = warp; t < TT; t += kWarps) {
+            if (t0 + t >= p.M) continue;
+            double x = 0.0;
+            for (int a = lane; a < gs; a += 32) {
+                const double re = cre[a * LD + t], im = cim[a * LD + t];
+                x += re * re + im * im;
+            }
+            x = warp_sum(x);
+            wx += x;
+            wx2 += x * x;
+        }
+        if (lane == 0) {
+            obs[2 * warp] = wx;
+            obs[2 * warp + 1] = wx2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0, s2 = 0.0;
+            for (int w = 0; w < kWarps; ++w) {
+                s += obs[2 * w];
+                s2 += obs[2 * w + 1];
+            }
+            p.obs_part[((size_t)blockIdx.x * K + g) * 2] = s;
+            p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = s2;
+        }
+    };
+    auto half_all = [&](int g, int half) {
+        for (int t = warp; t < TT; t += kWarps) {
+            if (t0 + t >= p.M) continue;
+            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, y64, lane);
+        }
+    };
+
+    load_grid(0);
+    __syncthreads();
+    observe(0, gs0);
+    half_all(0, 1);
+
+    const int tx = tid % TXN, ty = tid / TXN;
+    for (int g = 1; g < K; ++g) {
+        // ---- rotation c <- O_{g-1} c ---------------------------------------------
+        R accr[RA][4], acci[RA][4];
+#pragma unroll
+        for (int i = 0; i < RA; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = (R)0;
+        const R *OT = reinterpret_cast<const R *>(p.tab.OT) + (size_t)(g - 1) * N * N;
+        for (int b0 = 0; b0 < N; b0 += KB) {
+            __syncthreads();
+            for (int i = tid; i < KB * N; i += kThreads) osm[i] = OT[(size_t)b0 * N + i];
+            __syncthreads();
+            for (int bb = 0; bb < KB; ++bb) {
+                R vr[4], vi[4];
+                Vec4<R>::load(&cre[(b0 + bb) * LD + 4 * tx], vr);
+                Vec4<R>::load(&cim[(b0 + bb) * LD + 4 * tx], vi);
+#pragma unroll
+                for (int i = 0; i < RA; ++i) {
+                    const int a = ty + i * TYN;
+                    const R o = a < N ? osm[bb * N + a] : (R)0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        accr[i][j] = fma(o, vr[j], accr[i][j]);
+                        acci[i][j] = fma(o, vi[j], acci[i][j]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < RA; ++i) {
+            const int a = ty + i * TYN;
+            if (a < N) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cre[a * LD + 4 * tx + j] = accr[i][j];
+                    cim[a * LD + 4 * tx + j] = acci[i][j];
+                }
+            }
+        }
+        load_grid(g);
+        __syncthreads();
+        // ---- epilogue: half-step into s_g, observe, half-step out of s_g ------------
+        half_all(g, 0);
+        __syncthreads();
+        observe(g, p.tab.meta[g].gs_size);
+        if (g < K - 1) half_all(g, 1);
+    }
+    __syncthreads();
+    for (int i = tid; i < N * TT; i += kThreads) {
+        const int t = i / N, a = i % N;
+        if (t0 + t < p.M) {
+            p.final_state[((size_t)(t0 + t) * N + a) * 2] = (double)cre[a * LD + t];
+            p.final_state[((size_t)(t0 + t) * N + a) * 2 + 1] = (double)cim[a * LD + t];
+        }
+    }
+}
+
+__global__ void reduce_obs(const double *part, double *sum, int n_cta, int K) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= K) return;
+    double s = 0.0, s2 = 0.0;
+    for (int c = 0; c < n_cta; ++c) {
+        s += part[((size_t)c * K + g) * 2];
+        s2 += part[((size_t)c * K + g) * 2 + 1];
+    }
+    sum[2 * g] = s;
+    sum[2 * g + 1] = s2;
+}
+
+template <typename R, int RA>
+int launch_simt(const RunParams &p, cudaStream_t st, size_t smem) {
+    auto kern = propagate_simt<R, RA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    kern<<<p.n_cta, kThreads, smem, st>>>(p);
+    return (int)cudaGetLastError();
+}
+
+template <typename R>
+int launch_prec(const RunParams &p, cudaStream_t st, size_t smem) {
+    switch (p.RA) {
+        case 1: return launch_simt<R, 1>(p, st, smem);
+        case 2: return launch_simt<R, 2>(p, st, smem);
+        case 4: return launch_simt<R, 4>(p, st, smem);
+        case 8: return launch_simt<R, 8>(p, st, smem);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+size_t simt_smem_bytes(int N, int TT, int precision) {
+    const size_t rs = precision == AQT_PREC_FP64 ? 8 : 4;
+    const int LD = TT + 4;
+    const int KB = std::min(N, std::max(1, kChunkBytes / (int)(N * rs)));
+    size_t b = 0;
+    b += (size_t)N * 8 + 2 * (size_t)TT * 8 + 2 * kWarps * 8;  // d2s, logr, ell, obs
+    b += (size_t)((TT + 3) & ~3) * 4;                           // nj
+    b += 2 * (size_t)N * LD * rs;                               // cre, cim
+    b += (size_t)KB * N * rs;                                   // O chunk
+    b += 2 * (size_t)N * rs;                                    // eh
+    return b;
+}
+
+// Pick trajectories per CTA (TT) and GEMM rows per thread (RA) so that
+// TT/4 * (256 / (TT/4)) threads cover N rows with RA <= 8 and the grid has
+// at least two CTAs per SM when M allows.
+void simt_shape(int N, int64_t M, int precision, int num_sms, int *TT, int *RA) {
+    const int cands[] = {64, 32, 16, 8, 4};
+    int best_tt = 4, best_ra = 8;
+    for (int tt : cands) {
+        const int tyn = kThreads / (tt / 4);
+        int ra = 1;
+        while (ra * tyn < N) ra *= 2;
+        if (ra > 8) continue;
+        if (simt_smem_bytes(N, tt, precision) > 200 * 1024) continue;
+        best_tt = tt;
+        best_ra = ra;
+        if ((M + tt - 1) / tt >= 2LL * num_sms) break;
+    }
+    *TT = best_tt;
+    *RA = best_ra;
+}
+
+int launch_run(const RunParams &p, int precision, void *stream, size_t smem) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = precision == AQT_PREC_FP64 ? launch_prec<double>(p, st, smem) : launch_prec<float>(p, st, smem);
+    if (e) return e;
+    reduce_obs<<<(p.K + 127) / 128, 128, 0, st>>>(p.obs_part, p.obs_sum, p.n_cta, p.K);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace aqt

@@ -1,0 +1,289 @@
+// FP64 host tables for the AME trajectory path, one set per grid point s_g.
+//
+// arXiv:1710.03431: H_S(s) of Sec. V (Eq. H_S); Lindblad operators of Sec. II
+// (Eq. Lindblad2) with independent sz baths (Sec. V; App. F), rates absorbed
+// (Sec. III, Eq. Aired); effective Hamiltonian of Sec. III (Eq. Heff) with the
+// Lamb shift of App. E. In the instantaneous eigenframe (columns of V_g) the
+// state is a coefficient vector c (psi = V_g c), and with
+//   M_alpha = V^T sz_alpha V,   w_ab = E(m(b)) - E(m(a)),   f = S - (i/2) gamma,
+// the eigenframe H_eff is block diagonal over degenerate manifolds:
+//   K[b,b'] = eps_b delta_bb' + sum_alpha sum_a f(w_ab) M_alpha[a,b] M_alpha[a,b'].
+// The library requires K to be diagonal (true whenever every manifold is a
+// single level, and at s = 0 of the transverse-field Ising model where each
+// block is a multiple of the identity); otherwise it reports AQT_EDEGEN.
+//
+// Readings shared with the test oracle (which implements them separately):
+// manifolds chain consecutive eigenvalues within tol = 1e-9 max(1, max|eps|)
+// and take the mean energy; Bohr frequencies use manifold energies; classes of
+// equal Bohr frequency chain within tol and must be tight (spread <= tol).
+#include "aqt_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <thread>
+
+namespace aqt {
+
+namespace {
+
+unsigned n_threads() {
+    unsigned h = std::thread::hardware_concurrency();
+    return std::max(1u, std::min(64u, h));
+}
+
+template <class F>
+void parallel_for(int count, F f) {
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    const unsigned nt = std::min<unsigned>(n_threads(), (unsigned)std::max(count, 1));
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (int i = next++; i < count; i = next++) f(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+void schedule_at(const Inputs &in, double s, double *A, double *B) {
+    const auto &ks = in.ks;
+    size_t j = 0;
+    while (j + 2 < ks.size() && s > ks[j + 1]) ++j;
+    const double u = (s - ks[j]) / (ks[j + 1] - ks[j]);
+    *A = in.kA[j] + u * (in.kA[j + 1] - in.kA[j]);
+    *B = in.kB[j] + u * (in.kB[j + 1] - in.kB[j]);
+}
+
+}  // namespace
+
+aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
+    const int n = in.n, N = 1 << n, K = in.K;
+    tab.n = n;
+    tab.N = N;
+    tab.K = K;
+    tab.dt = in.t_f / (K - 1);
+    tab.tau = 0.5 * tab.dt;
+    const size_t NN = (size_t)N * N;
+    tab.evals.assign((size_t)K * N, 0.0);
+    tab.V.assign((size_t)K * NN, 0.0);
+    tab.kdiag.assign((size_t)K * N * 2, 0.0);
+    tab.ehalf.assign((size_t)K * N * 2, 0.0);
+    tab.d2.assign((size_t)K * N, 0.0);
+    tab.G.assign((size_t)K * n * N, 0.0);
+    tab.M.assign((size_t)K * n * NN, 0.0);
+    tab.lvlE.assign((size_t)K * N, 0.0);
+    tab.mfirst.assign((size_t)K * N, 0);
+    tab.msize.assign((size_t)K * N, 0);
+    tab.meta.assign(K, GridMeta{0, 1, 0.0});
+    tab.OT.assign((size_t)(K - 1) * NN, 0.0);
+
+    // classical energies sum_i hz_i z_i + sum_{i<j} J_ij z_i z_j, z = 1 - 2 bit
+    std::vector<double> Ez(N, 0.0);
+    std::vector<int8_t> z((size_t)n * N);
+    for (int x = 0; x < N; ++x) {
+        double e = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int zi = 1 - 2 * ((x >> i) & 1);
+            z[(size_t)i * N + x] = (int8_t)zi;
+            e += in.hz[i] * zi;
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                e += in.J[(size_t)i * n + j] * (1 - 2 * ((x >> i) & 1)) * (1 - 2 * ((x >> j) & 1));
+        Ez[x] = e;
+    }
+
+    std::mutex mu;
+    aqt_status st = AQT_OK;
+    auto fail = [&](aqt_status s, const std::string &m) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (st == AQT_OK) {
+            st = s;
+            *err = m;
+        }
+    };
+
+    // ---- pass 1: eigensystems ----------------------------------------------
+    parallel_for(K, [&](int g) {
+        const double s = (double)g / (K - 1);
+        double A, B;
+        schedule_at(in, s, &A, &B);
+        std::vector<double> H(NN, 0.0);
+        for (int x = 0; x < N; ++x) {
+            H[(size_t)x * N + x] = B * Ez[x];
+            for (int i = 0; i < n; ++i) H[(size_t)x * N + (x ^ (1 << i))] = -A;
+        }
+        if (!sym_eigen(N, H.data(), &tab.evals[(size_t)g * N], &tab.V[(size_t)g * NN]))
+            fail(AQT_ENOCONV, "eigensolver did not converge at grid point " + std::to_string(g));
+    });
+    if (st != AQT_OK) return st;
+
+    double wmax = 10.0;
+    for (int g = 0; g < K; ++g)
+        wmax = std::max(wmax, tab.evals[(size_t)g * N + N - 1] - tab.evals[(size_t)g * N]);
+    Bath bath = in.bath;
+    bath.build_lamb(wmax * 1.05 + 1.0);
+
+    // ---- pass 2: manifolds, M_alpha, rates, H_eff ----------------------------
+    parallel_for(K, [&](int g) {
+        const double *ev = &tab.evals[(size_t)g * N];
+        const double *V = &tab.V[(size_t)g * NN];
+        double emax = 1.0;
+        for (int a = 0; a < N; ++a) emax = std::max(emax, std::fabs(ev[a]));
+        const double tol = 1e-9 * emax;
+        GridMeta &meta = tab.meta[g];
+        meta.tol = tol;
+        double *lvlE = &tab.lvlE[(size_t)g * N];
+        int32_t *mf = &tab.mfirst[(size_t)g * N];
+        int32_t *ms = &tab.msize[(size_t)g * N];
+        std::vector<int> first;  // first level of each manifold
+        for (int a = 0; a < N; ++a)
+            if (a == 0 || ev[a] - ev[a - 1] > tol) first.push_back(a);
+        first.push_back(N);
+        std::vector<double> E(first.size() - 1);
+        meta.degenerate = 0;
+        for (size_t m = 0; m + 1 < first.size(); ++m) {
+            double acc = 0.0;
+            for (int a = first[m]; a < first[m + 1]; ++a) acc += ev[a];
+            const int sz = first[m + 1] - first[m];
+            E[m] = acc / sz;
+            if (sz > 1) meta.degenerate = 1;
+            for (int a = first[m]; a < first[m + 1]; ++a) {
+                lvlE[a] = E[m];
+                mf[a] = first[m];
+                ms[a] = sz;
+            }
+        }
+        meta.gs_size = first[1] - first[0];
+        if (g == 0 && meta.gs_size != 1) {
+            fail(AQT_EDEGEN, "ground state of H_S(0) is degenerate: the initial state is ambiguous");
+            return;
+        }
+        // Bohr classes over manifold pairs must be tight chains.
+        {
+            const size_t nm = E.size();
+            std::vector<double> w;
+            w.reserve(nm * (nm - 1));
+            for (size_t ma = 0; ma < nm; ++ma)
+                for (size_t mb = 0; mb < nm; ++mb)
+                    if (ma != mb) w.push_back(E[mb] - E[ma]);
+            std::sort(w.begin(), w.end());
+            size_t st0 = 0;
+            for (size_t i = 1; i <= w.size(); ++i) {
+                if (i == w.size() || w[i] - w[i - 1] > tol) {
+                    if (i > 0 && w[i - 1] - w[st0] > tol) {
+                        fail(AQT_EDEGEN, "ambiguous Bohr-frequency grouping at grid point " + std::to_string(g));
+                        return;
+                    }
+                    st0 = i;
+                }
+            }
+        }
+        // VT rows are eigenvectors
+        std::vector<double> VT(NN), Y(NN);
+        for (int x = 0; x < N; ++x)
+            for (int a = 0; a < N; ++a) VT[(size_t)a * N + x] = V[(size_t)x * N + a];
+        double *Mg = &tab.M[(size_t)g * n * NN];
+        for (int al = 0; al < n; ++al) {
+            const int8_t *za = &z[(size_t)al * N];
+            for (int a = 0; a < N; ++a)
+                for (int x = 0; x < N; ++x) Y[(size_t)a * N + x] = VT[(size_t)a * N + x] * za[x];
+            double *Ma = Mg + (size_t)al * NN;
+            for (int a = 0; a < N; ++a) {
+                const double *ya = &Y[(size_t)a * N];
+                for (int b = a; b < N; ++b) {
+                    const double *vb = &VT[(size_t)b * N];
+                    double acc = 0.0;
+                    for (int x = 0; x < N; ++x) acc += ya[x] * vb[x];
+                    Ma[(size_t)a * N + b] = acc;
+                    Ma[(size_t)b * N + a] = acc;
+                }
+            }
+        }
+        // rates: gamma and S per level pair (a <- b), reused over alpha
+        std::vector<double> gam(NN), lam(NN);
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) {
+                const double w = lvlE[b] - lvlE[a];
+                gam[(size_t)a * N + b] = bath.gamma(w);
+                lam[(size_t)a * N + b] = bath.lamb(w);
+            }
+        double *Gg = &tab.G[(size_t)g * n * N];
+        double *kd = &tab.kdiag[(size_t)g * N * 2];
+        for (int b = 0; b < N; ++b) {
+            kd[2 * b] = ev[b];
+            kd[2 * b + 1] = 0.0;
+        }
+        for (int al = 0; al < n; ++al) {
+            const double *Ma = Mg + (size_t)al * NN;
+            for (int a = 0; a < N; ++a) {
+                const double *row = Ma + (size_t)a * N;  // M[a][b] over b
+                for (int b = 0; b < N; ++b) {
+                    const double m2 = row[b] * row[b];
+                    const double gm = gam[(size_t)a * N + b];
+                    Gg[(size_t)al * N + b] += gm * m2;
+                    kd[2 * b] += lam[(size_t)a * N + b] * m2;
+                    kd[2 * b + 1] -= 0.5 * gm * m2;
+                }
+            }
+        }
+        // degenerate manifolds: the off-diagonal block of K must vanish
+        if (meta.degenerate) {
+            const double ktol = 1e-12 * emax;
+            for (size_t m = 0; m + 1 < first.size(); ++m) {
+                for (int b = first[m]; b < first[m + 1]; ++b)
+                    for (int bp = b + 1; bp < first[m + 1]; ++bp) {
+                        double re = 0.0, im = 0.0;
+                        for (int al = 0; al < n; ++al) {
+                            const double *Ma = Mg + (size_t)al * NN;
+                            for (int a = 0; a < N; ++a) {
+                                const double mm = Ma[(size_t)a * N + b] * Ma[(size_t)a * N + bp];
+                                re += lam[(size_t)a * N + b] * mm;
+                                im -= 0.5 * gam[(size_t)a * N + b] * mm;
+                            }
+                        }
+                        if (std::hypot(re, im) > ktol) {
+                            fail(AQT_EDEGEN, "effective Hamiltonian is not diagonal inside a degenerate "
+                                             "manifold at grid point " + std::to_string(g));
+                            return;
+                        }
+                    }
+            }
+        }
+        // half-step factors exp(-i K tau) and |.|^2
+        double *eh = &tab.ehalf[(size_t)g * N * 2];
+        double *dd = &tab.d2[(size_t)g * N];
+        for (int b = 0; b < N; ++b) {
+            const double re = kd[2 * b], im = kd[2 * b + 1];
+            const double amp = std::exp(im * tab.tau);
+            eh[2 * b] = amp * std::cos(re * tab.tau);
+            eh[2 * b + 1] = -amp * std::sin(re * tab.tau);
+            dd[b] = std::exp(2.0 * im * tab.tau);
+        }
+    });
+    if (st != AQT_OK) return st;
+
+    // ---- pass 3: frame rotations OT_g[b][a] = (V_g^T V_{g+1})[b][a] ------------
+    parallel_for(K - 1, [&](int g) {
+        const double *V0 = &tab.V[(size_t)g * NN];
+        const double *V1 = &tab.V[(size_t)(g + 1) * NN];
+        std::vector<double> T0(NN), T1(NN);
+        for (int x = 0; x < N; ++x)
+            for (int a = 0; a < N; ++a) {
+                T0[(size_t)a * N + x] = V0[(size_t)x * N + a];
+                T1[(size_t)a * N + x] = V1[(size_t)x * N + a];
+            }
+        double *OT = &tab.OT[(size_t)g * NN];
+        for (int b = 0; b < N; ++b)
+            for (int a = 0; a < N; ++a) {
+                const double *u = &T0[(size_t)b * N];
+                const double *v = &T1[(size_t)a * N];
+                double acc = 0.0;
+                for (int x = 0; x < N; ++x) acc += u[x] * v[x];
+                OT[(size_t)b * N + a] = acc;
+            }
+    });
+    return AQT_OK;
+}
+
+}  // namespace aqt

@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI (no GPU): symbols, argument validation, and
+the FP64 tables built by the library against the oracle."""
+import math
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lindblad
+
+
+def _declared_symbols():
+    hdr = open(__file__.replace("tests/test_capi_host.py", "include/aqt.h")).read()
+    return sorted(set(re.findall(r"\b(aqt_[a-z_]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol(aqt_lib):
+    lib = aqt_lib.lib()
+    syms = _declared_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(aqt_lib.EXPORTS)
+
+
+def _host_ctx(A, inst, M=10, precision=0):
+    c = A.aqt_create(-1)
+    A.aqt_set_ising(c, inst.n_qubits, inst.hz, inst.J)
+    A.aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
+    A.aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
+    A.aqt_set_grid(c, inst.t_f, inst.n_grid)
+    A.aqt_set_trajectories(c, M, 1, precision, 16)
+    return c
+
+
+def test_argument_validation(aqt_lib):
+    A = aqt_lib
+    c = A.aqt_create(-1)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_set_ising(c, 0, [1.0], [0.0])
+    assert e.value.status == A.AQT_EINVAL
+    with pytest.raises(A.AqtError):
+        A.aqt_set_ising(c, 11, np.zeros(11), np.zeros(121))
+    with pytest.raises(A.AqtError):
+        A.aqt_set_schedule(c, [0.0, 0.5], [1, 1], [0, 1])          # does not reach 1
+    with pytest.raises(A.AqtError):
+        A.aqt_set_schedule(c, [0.0, 0.6, 0.5, 1.0], [1] * 4, [0] * 4)
+    with pytest.raises(A.AqtError):
+        A.aqt_set_bath(c, 1e-3, 0.0, 1.0, 1)
+    with pytest.raises(A.AqtError):
+        A.aqt_set_grid(c, 10.0, 1)
+    with pytest.raises(A.AqtError):
+        A.aqt_set_trajectories(c, 0, 1, 0, 10)
+    with pytest.raises(A.AqtError):
+        A.aqt_set_trajectories(c, 10, 1, 7, 10)
+    with pytest.raises(A.AqtError):
+        A.aqt_workspace_size(c)                                       # inputs incomplete
+    with pytest.raises(A.AqtError):
+        A.aqt_set_ising(c, 2, [np.nan, 0.0], np.zeros(4))
+    A.aqt_destroy(c)
+    with pytest.raises(A.AqtError):
+        A.aqt_create(-2)
+
+
+def test_host_context_cannot_run(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(2, 3, n_grid=5)
+    c = _host_ctx(A, inst)
+    assert A.aqt_workspace_size(c) > 0
+    A.aqt_build_tables(c, 0)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_run(c, 0)
+    assert e.value.status == A.AQT_ENODEV
+    A.aqt_destroy(c)
+
+
+@pytest.mark.parametrize("n,seed,s_idx", [(3, 7, [0, 4, 10]), (4, 1710_03431, [0, 1, 7, 10])])
+def test_tables_match_oracle(aqt_lib, n, seed, s_idx):
+    A = aqt_lib
+    inst = W.tfim_instance(n, seed, n_grid=11)
+    N = 1 << n
+    c = _host_ctx(A, inst)
+    A.aqt_build_tables(c, 0)
+    for g in s_idx:
+        fr = lindblad.Frame(inst, g / 10)
+        ev = A.aqt_debug_table(c, 0, g, (N,))
+        np.testing.assert_allclose(ev, fr.eig.evals, atol=1e-12)
+        kd = A.aqt_debug_table(c, 1, g, (N, 2))
+        Kd = kd[:, 0] + 1j * kd[:, 1]
+        np.testing.assert_allclose(Kd.imag, np.diag(fr.K).imag, atol=1e-13)
+        np.testing.assert_allclose(Kd.real, np.diag(fr.K).real, atol=1e-8)   # Lamb-shift tables
+        V = A.aqt_debug_table(c, 5, g, (N, N))
+        assert np.max(np.abs(V.T @ V - np.eye(N))) < 1e-13
+        H = V @ np.diag(ev) @ V.T
+        Ho = fr.eig.V @ np.diag(fr.eig.evals) @ fr.eig.V.T
+        assert np.max(np.abs(H - Ho)) < 1e-12
+        if fr.eig.nondegenerate:
+            Ml = A.aqt_debug_table(c, 3, g, (n, N, N))
+            assert np.max(np.abs(np.abs(Ml) - np.abs(fr.M))) < 1e-12
+            G = A.aqt_debug_table(c, 2, g, (n, N))
+            Go = np.sum(fr.gam[None] * fr.M ** 2, axis=1)
+            np.testing.assert_allclose(G, Go, rtol=1e-11, atol=1e-16)
+        if g < 10:
+            O = A.aqt_debug_table(c, 4, g, (N, N))
+            V1 = A.aqt_debug_table(c, 5, g + 1, (N, N))
+            assert np.max(np.abs(O - V1.T @ V)) < 1e-13
+    A.aqt_destroy(c)
+
+
+def test_degenerate_ground_state_rejected(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(2, 3, n_grid=5)
+    inst.sched_A = np.array([0.0, 0.0])       # H(0) = 0: fully degenerate start
+    c = _host_ctx(A, inst)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_build_tables(c, 0)
+    assert e.value.status == A.AQT_EDEGEN
