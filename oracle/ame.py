@@ -28,7 +28,7 @@ def spectral_bound(inst) -> float:
     hz_sum = float(np.sum(np.abs(inst.hz)))
     j_sum = float(np.sum(np.abs(np.triu(inst.J, 1))))
     r = max(abs(a) * n + abs(b) * (hz_sum + j_sum) for a, b in zip(inst.sched_A, inst.sched_B))
-    return 2.0 * r
+    return 2.0 * r * 1.01 + 1.0
 
 
 def frames(inst):

@@ -10,7 +10,7 @@ Sec. II, Eq. Lindblad2: the Lindblad operators are built from the instantaneous
 eigenstates and group level pairs by equal Bohr frequency. Readings (the paper
 states exact equality only):
   * levels are sorted ascending; consecutive eigenvalues closer than
-    tol = 1e-9 * max(1, max|eps|) form one degenerate manifold, whose energy is
+    tol = 1e-12 * max(1, max|eps|) form one degenerate manifold, whose energy is
     the mean of its eigenvalues;
   * the Bohr frequency of a level pair (a, b) is E(m(b)) - E(m(a)); pairs in the
     same manifold have omega = 0;
@@ -67,7 +67,7 @@ def grid(inst):
 
 
 def energy_tol(evals: np.ndarray) -> float:
-    return 1e-9 * max(1.0, float(np.max(np.abs(evals))))
+    return 1e-12 * max(1.0, float(np.max(np.abs(evals))))
 
 
 class Eigen:

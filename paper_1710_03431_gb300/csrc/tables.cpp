@@ -13,7 +13,7 @@
 // block is a multiple of the identity); otherwise it reports AQT_EDEGEN.
 //
 // Readings shared with the test oracle (which implements them separately):
-// manifolds chain consecutive eigenvalues within tol = 1e-9 max(1, max|eps|)
+// manifolds chain consecutive eigenvalues within tol = 1e-12 max(1, max|eps|)
 // and take the mean energy; Bohr frequencies use manifold energies; classes of
 // equal Bohr frequency chain within tol and must be tight (spread <= tol).
 #include "aqt_internal.h"
@@ -130,7 +130,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         const double *V = &tab.V[(size_t)g * NN];
         double emax = 1.0;
         for (int a = 0; a < N; ++a) emax = std::max(emax, std::fabs(ev[a]));
-        const double tol = 1e-9 * emax;
+        const double tol = 1e-12 * emax;
         GridMeta &meta = tab.meta[g];
         meta.tol = tol;
         double *lvlE = &tab.lvlE[(size_t)g * N];
