@@ -56,6 +56,8 @@ def lamb_shift_direct(omega: float, eta_g2: float, omega_c: float, beta: float) 
     g0 = gamma(omega, eta_g2, omega_c, beta)
 
     def f(x):
+        if x == omega:   # removable point of the subtracted integrand (measure zero)
+            return 0.0
         return (gamma(x, eta_g2, omega_c, beta) - g0) / (omega - x)
 
     pts = sorted(set(p for p in (omega, 0.0, -omega_c, omega_c) if -L < p < L))

@@ -29,6 +29,13 @@ def run_lib(A, inst, precision, M=None, jcap=None):
     return dict(status=status, mean=mean, se=se, s1=s1, s2=s2, jumps=jumps, dropped=dropped, final=final)
 
 
+def se_bound(ref, M):
+    """Upper bound on the standard error of a mean of M values in [0, 1] whose
+    mean is ref: var <= ref (1 - ref). The sample error underestimates the true
+    one when excitations are rare events (none may have happened yet)."""
+    return math.sqrt(max(ref * (1.0 - ref), 0.0) / M)
+
+
 def jumps_by_traj(recs):
     out = {}
     for r in recs:
@@ -92,7 +99,7 @@ def test_three_qubit_fp64_and_ame(aqt_lib):
     np.testing.assert_allclose(res["s1"], p.sum(axis=0), atol=1e-8)
     ref = ame.run(inst)["p_gs"]
     for k in (50, 100, 150, 200):
-        assert abs(res["mean"][k] - ref[k]) < 3.5 * res["se"][k] + 1e-9
+        assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], se_bound(ref[k], M)) + 1e-9
 
 
 def test_cfg_small_fp64_full(aqt_lib):
@@ -107,7 +114,8 @@ def test_cfg_small_fp64_full(aqt_lib):
     ref = ame.run(inst)["p_gs"]
     pts = [250, 500, 750, 999]
     for k in pts:
-        assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], 1e-4), (k, res["mean"][k], ref[k])
+        tol = 3.5 * max(res["se"][k], se_bound(ref[k], inst.M))
+        assert abs(res["mean"][k] - ref[k]) < tol, (k, res["mean"][k], ref[k], tol)
 
 
 def test_fp32_against_oracle(aqt_lib):
@@ -120,7 +128,7 @@ def test_fp32_against_oracle(aqt_lib):
     assert np.max(np.abs(res["s1"] - p.sum(axis=0))) < 1e-3 * M
     ref = ame.run(inst)["p_gs"]
     for k in (100, 200):
-        assert abs(res["mean"][k] - ref[k]) < 3.5 * res["se"][k] + 1e-6
+        assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], se_bound(ref[k], M)) + 1e-6
 
 
 def test_repeatable_and_overflow(aqt_lib):
