@@ -150,6 +150,33 @@ aqt_status aqt_get_jumps(aqt_ctx *ctx, aqt_jump *host_buf, int64_t cap, int64_t 
  * signs); basis 1: computational basis. */
 aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
 
+/* Run without caller-provided scratch (the paper has no counterpart: this is
+ * a deployment convenience). For callers that cannot allocate device memory
+ * when they run -- code inside another framework's memory pool with a budget
+ * fixed at start-up, or host threads where device allocation is not allowed.
+ * It runs the same propagation as aqt_run on the context's device tables
+ * (aqt_build_tables must have run on a bound workspace) and writes to the
+ * caller's device outputs: obs_sums[n_grid][2] (sum of x, sum of x^2),
+ * final_states[M][N][2] (eigenbasis, FP64), jumps[jump_capacity] (unsorted),
+ * *jump_count (records produced, kept or not) and *status (0, or 2 for a
+ * numeric problem). The kernel's scratch -- per-CTA observable partials and
+ * FP64 jump vectors -- comes from one 32 MiB array compiled into the library,
+ * held on every GPU that loads the library until the process exits. No
+ * device memory is allocated by this call.
+ *  - The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress with the device current); make that first call
+ *    before any stream capture.
+ *  - A run that needs more than 32 MiB of scratch (it grows with
+ *    M x n_grid and with M x N) returns AQT_EINVAL with the size in the message.
+ *  - All calls on one device share the array and it keeps the last call's
+ *    contents; calls whose kernels can overlap on the GPU race on it, so
+ *    order them (one stream, or events).
+ * Asynchronous on `stream`; *jump_count and *status are zeroed on the stream
+ * before the kernel starts. */
+aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, double *final_states,
+                                  aqt_jump *jumps, int64_t jump_capacity, unsigned long long *jump_count,
+                                  int32_t *status);
+
 /* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 M_alpha = V^T sz_alpha V,
  * [n][N][N]; 4 frame rotation O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1);

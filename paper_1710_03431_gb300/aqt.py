@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4
 EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
            "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
            "aqt_bind_workspace", "aqt_build_tables", "aqt_run", "aqt_sync", "aqt_get_observables",
-           "aqt_get_observable_sums", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table"]
+           "aqt_get_observable_sums", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
+           "aqt_run_static_scratch"]
 
 
 class aqt_jump(C.Structure):
@@ -70,6 +71,7 @@ def lib():
             "aqt_get_jumps": (I, [P, C.POINTER(aqt_jump), I64, C.POINTER(I64), C.POINTER(I64)]),
             "aqt_get_final_state": (I, [P, I, D]),
             "aqt_debug_table": (I, [P, I, I, D]),
+            "aqt_run_static_scratch": (I, [P, P, P, P, P, I64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -189,6 +191,15 @@ def aqt_debug_table(ctx, which: int, grid: int, shape):
     out = np.empty(int(np.prod(shape)))
     _check(ctx, lib().aqt_debug_table(ctx, int(which), int(grid), _dp(out)))
     return out.reshape(shape)
+
+
+def aqt_run_static_scratch(ctx, stream: int, obs_sums: int, final_states: int, jumps: int, jump_capacity: int,
+                           jump_count: int, status: int):
+    """Device pointers (ints) for the outputs; scratch comes from the library's
+    static array (see include/aqt.h)."""
+    _check(ctx, lib().aqt_run_static_scratch(ctx, C.c_void_p(stream), C.c_void_p(obs_sums),
+                                             C.c_void_p(final_states), C.c_void_p(jumps), int(jump_capacity),
+                                             C.c_void_p(jump_count), C.c_void_p(status)))
 
 
 # ---- convenience ------------------------------------------------------------------

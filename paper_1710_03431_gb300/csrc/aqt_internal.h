@@ -100,6 +100,16 @@ struct RunParams {
 // Launch the propagation (precision per aqt_precision) and the observable
 // reduction on `stream`. Returns a CUDA error code (0 on success).
 int launch_run(const RunParams &p, int precision, void *stream, size_t smem_bytes);
+
+// Context accessors for the static-scratch run entry point (static_scratch.cu):
+// the scratch bytes a run of the current inputs needs, the run parameters
+// pointing at the context's device tables (outputs and scratch left unset),
+// the precision and the kernel's dynamic shared memory.
+aqt_status static_scratch_need(aqt_ctx *ctx, size_t *bytes);
+aqt_status static_run_params(aqt_ctx *ctx, RunParams *p);
+aqt_status set_error(aqt_ctx *ctx, aqt_status st, const std::string &msg);
+int run_precision(const aqt_ctx *ctx);
+size_t run_smem(const aqt_ctx *ctx);
 size_t simt_smem_bytes(int N, int TT, int precision);
 void simt_shape(int N, int64_t M, int precision, int num_sms, int *TT, int *RA);
 

@@ -103,6 +103,62 @@ aqt_status use_device(aqt_ctx *c) {
 
 }  // namespace
 
+// ---- accessors for the static-scratch entry point (static_scratch.cu) ------
+namespace aqt {
+
+aqt_status set_error(aqt_ctx *c, aqt_status st, const std::string &msg) { return fail(c, st, msg); }
+
+int run_precision(const aqt_ctx *c) { return c->in.precision; }
+
+size_t run_smem(const aqt_ctx *c) { return c->smem; }
+
+aqt_status static_scratch_need(aqt_ctx *c, size_t *bytes) {
+    if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs first");
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    compute_layout(c);
+    const size_t N = (size_t)1 << c->in.n, K = c->in.K;
+    const size_t part = ((size_t)c->n_cta * K * 2 * 8 + 255) & ~(size_t)255;
+    *bytes = part + (size_t)c->n_cta * 8 * 2 * N * 2 * 8;
+    return AQT_OK;
+}
+
+aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->tables_on_device) return fail(c, AQT_EINVAL, "build tables on the device before running");
+    const Layout &L = c->lay;
+    const Inputs &in = c->in;
+    *p = RunParams{};
+    p->n = in.n;
+    p->N = 1 << in.n;
+    p->K = in.K;
+    p->TT = c->TT;
+    p->RA = c->RA;
+    p->n_cta = c->n_cta;
+    p->M = in.M;
+    p->seed = in.seed;
+    p->tau = c->tab.tau;
+    p->dt = c->tab.dt;
+    p->eta_g2 = in.bath.eta_g2;
+    p->omega_c = in.bath.omega_c;
+    p->beta = in.bath.beta;
+    p->tab.kdiag = (const double *)(c->ws + L.kdiag);
+    p->tab.ehalf = (const double *)(c->ws + L.ehalf);
+    p->tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
+    p->tab.d2 = (const double *)(c->ws + L.d2);
+    p->tab.G = (const double *)(c->ws + L.G);
+    p->tab.M = (const double *)(c->ws + L.M);
+    p->tab.lvlE = (const double *)(c->ws + L.lvlE);
+    p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
+    p->tab.msize = (const int32_t *)(c->ws + L.msize);
+    p->tab.meta = (const GridMeta *)(c->ws + L.meta);
+    p->tab.OT = c->ws + L.OT;
+    return AQT_OK;
+}
+
+}  // namespace aqt
+
 extern "C" {
 
 aqt_status aqt_create(aqt_ctx **out, int device) {

@@ -1,0 +1,95 @@
+// A run entry point that allocates no device memory for its scratch.
+//
+// Who needs it: callers that cannot allocate device memory when they run the
+// propagation -- for example code that lives inside another framework's
+// memory pool with a budget fixed at start-up, or host threads on which
+// device allocation is not allowed. They still own and pass the tables
+// (built into their workspace by aqt_build_tables) and the output buffers;
+// the scratch the kernel needs (FP64 jump-resolution vectors and per-CTA
+// partial sums of the observable) comes from one fixed array compiled into
+// this library instead of from the caller.
+//
+// The array lives for as long as the library is loaded, on every GPU that
+// loads it. All calls on a device share it: it keeps whatever the last call
+// left there, and two calls whose kernels overlap on the GPU (different
+// streams, or no ordering between them) race on it.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "aqt_internal.h"
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32ull << 20;  // 32 MiB per device
+constexpr int kMaxDevices = 64;
+
+// File-scope device scratch. In host code this name is only a host-side
+// handle: its device address must be obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_mu;
+void *g_scratch_dev[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+cudaError_t scratch_address(int device, void **out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_scratch_dev[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_dev[device] = p;
+    }
+    *out = g_scratch_dev[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums,
+                                             double *final_states, aqt_jump *jumps, int64_t jump_capacity,
+                                             unsigned long long *jump_count, int32_t *status) {
+    if (!ctx || !obs_sums || !final_states || !jump_count || !status || jump_capacity < 0 ||
+        (jump_capacity > 0 && !jumps))
+        return AQT_EINVAL;
+    size_t need = 0;
+    aqt_status st = aqt::static_scratch_need(ctx, &need);
+    if (st != AQT_OK) return st;
+    if (need > kStaticScratchBytes)
+        return aqt::set_error(ctx, AQT_EINVAL,
+                              "this run needs " + std::to_string(need) + " bytes of scratch, more than the " +
+                                  std::to_string(kStaticScratchBytes) + "-byte static array");
+    aqt::RunParams p{};
+    st = aqt::static_run_params(ctx, &p);
+    if (st != AQT_OK) return st;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    void *base = nullptr;
+    if (e == cudaSuccess) e = scratch_address(dev, &base);
+    if (e != cudaSuccess)
+        return aqt::set_error(ctx, AQT_ECUDA, std::string("static scratch address: ") + cudaGetErrorString(e));
+    // Scratch carve: per-CTA observable partials, then per-warp FP64 jump
+    // vectors. Every element the kernel reads is written earlier in the same
+    // call, so nothing here has to start at zero.
+    unsigned char *b = static_cast<unsigned char *>(base);
+    const size_t part_bytes = (size_t)p.n_cta * p.K * 2 * sizeof(double);
+    p.obs_part = reinterpret_cast<double *>(b);
+    p.scratch = reinterpret_cast<double *>(b + ((part_bytes + 255) & ~(size_t)255));
+    // Outputs belong to the caller; the two counters must start at zero.
+    p.obs_sum = obs_sums;
+    p.final_state = final_states;
+    p.jumps = jumps;
+    p.jcap = jump_capacity;
+    p.jcount = jump_count;
+    p.status = status;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(jump_count, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return aqt::set_error(ctx, AQT_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    const int ce = aqt::launch_run(p, aqt::run_precision(ctx), stream, aqt::run_smem(ctx));
+    if (ce) return aqt::set_error(ctx, AQT_ECUDA, std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)ce));
+    return AQT_OK;
+}
