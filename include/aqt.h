@@ -64,10 +64,11 @@ typedef enum {
 
 /* One jump. t is the jump time in ns; the jump happened while the generator
  * was frozen at grid point `grid`, in the half-step before s_grid (half = 0)
- * or after it (half = 1). alpha is the qubit whose sz caused it; src is the
- * lowest level of the source degenerate manifold and dst the target level
- * (instantaneous eigenbasis, ascending energy); omega = E(src) - E(dst) is
- * its Bohr frequency (rad/ns). */
+ * or after it (half = 1). alpha is the qubit whose sz caused it; src and dst
+ * are the lowest levels of the source and target degenerate manifolds
+ * (instantaneous eigenbasis, ascending energy; a level inside a degenerate
+ * manifold depends on the arbitrary eigenbasis, the manifold does not);
+ * omega = E(src) - E(dst) is its Bohr frequency (rad/ns). */
 typedef struct {
     int32_t traj, grid, half, alpha, src, dst;
     double t, omega;

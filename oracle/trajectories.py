@@ -23,7 +23,11 @@ Readings shared with the CUDA path:
     class containing (a, m) is the channel; the sum of its units' weights is
     <A^dag A>, so each channel is drawn with probability Pi_i exactly. The new
     state is A_{alpha,class} psi, normalised;
-  * random numbers come from ``philox`` with the stream layout stated there.
+  * random numbers come from ``philox`` with the stream layout stated there;
+  * a jump record names the source and target manifolds by their lowest
+    level: inside a degenerate manifold the level that stage two lands on
+    depends on the arbitrary eigenbasis, the manifold (hence the channel and
+    the new state) does not.
 """
 from __future__ import annotations
 
@@ -118,7 +122,8 @@ class Trajectory:
             eig = piece.fr.eig
             self.jumps.append(dict(traj=self.traj, grid=grid_index, half=half,
                                    t=t0 + elapsed + tstar, alpha=al,
-                                   src=int(eig.manifolds[m][0]), dst=a,
+                                   src=int(eig.manifolds[m][0]),
+                                   dst=int(eig.manifolds[eig.level_manifold[a]][0]),
                                    omega=float(eig.E[m] - eig.E[eig.level_manifold[a]])))
             self.r = rnext
             elapsed += tstar

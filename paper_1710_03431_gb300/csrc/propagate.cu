@@ -300,7 +300,7 @@ __device__ void resolve_half(const RunParams &p, int g, int half, int64_t traj, 
                 rec.half = half;
                 rec.alpha = al_s;
                 rec.src = bsrc;
-                rec.dst = adst;
+                rec.dst = mfirst[adst];
                 rec.t = t_jump;
                 rec.omega = wstar;
                 p.jumps[idx] = rec;
