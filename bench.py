@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="f16split", choices=["f16split", "fp32", "fp64"])
     ap.add_argument("--tf", type=float, default=10.0)
     ap.add_argument("--M", type=int, default=10_000)
     ap.add_argument("--n-grid", type=int, default=2000)
@@ -205,7 +205,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     inst = workload(args)
-    prec = A.AQT_PREC_FP32 if args.precision == "fp32" else A.AQT_PREC_FP64
+    prec = {"fp32": A.AQT_PREC_FP32, "fp64": A.AQT_PREC_FP64, "f16split": A.AQT_PREC_F16SPLIT}[args.precision]
     seed = inst.seed + rank
     sess = A.Session(inst, precision=prec, device=local, seed=seed)
     t0 = time.perf_counter()
@@ -274,9 +274,10 @@ def run_ours(args):
         e2e_s = (time.perf_counter() - t1) / args.e2e_steps
         A.aqt_destroy(ctx2)
         rs = 8 if prec == A.AQT_PREC_FP64 else 4
+        tcl = K * N * 16 if prec == A.AQT_PREC_F16SPLIT else 0
         n = inst.n_qubits
         h2d = (K * N * (2 * 8 + 2 * 8 + 2 * 4 + 8 + 8 + 4 + 4) + K * n * N * 8 + K * n * N * N * 8 + K * 16
-               + (K - 1) * N * N * rs)
+               + (K - 1) * N * N * rs + tcl)
         e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(K * 2 * 8 + 12), "seconds_per_step": e2e_s,
                "includes": "set_* + FP64 host table build + H2D + run + sync + observables D2H"}
@@ -288,28 +289,41 @@ def run_ours(args):
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     flops = 4.0 * N * N * traj_steps
     mhz = ck.get("sm_max_mhz") or 2070.0
-    if prec == A.AQT_PREC_FP32:
-        peak = alu_fp32_peak_tflops(num_sms, mhz)
-        peak_src = f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
-    else:
-        peak = alu_fp64_peak_tflops(num_sms, mhz)
-        peak_src = f"FP64: 1.25 TFLOP/s nominal scaled to {mhz:.0f} MHz"
     achieved = flops / kern_avg_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"propagate_simt<{'float' if prec else 'double'}>",
-            "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state)",
-            "peak_source": peak_src}
+    if prec == A.AQT_PREC_F16SPLIT:
+        peaks, src = measured_peaks()
+        peak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "propagate_tc",
+                "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state); "
+                               "the split form issues 3x that on the FP16 tensor pipe",
+                "issued_mma_frac": 3.0 * achieved / peak,
+                "peak_source": f"dense bf16/fp16 tensor peak, burst, {src} (MEASURED_PEAKS.json bf16_tflops; "
+                               "fp16 runs at the bf16 rate)"}
+    else:
+        if prec == A.AQT_PREC_FP32:
+            peak = alu_fp32_peak_tflops(num_sms, mhz)
+            peak_src = f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+        else:
+            peak = alu_fp64_peak_tflops(num_sms, mhz)
+            peak_src = f"FP64: 1.25 TFLOP/s nominal scaled to {mhz:.0f} MHz"
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"propagate_simt<{'float' if prec else 'double'}>",
+                "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state)",
+                "peak_source": peak_src}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == A.AQT_PREC_FP32 else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {A.AQT_PREC_FP32: "f32", A.AQT_PREC_FP64: "f64",
+                                       A.AQT_PREC_F16SPLIT: "f16x3-f32acc"}[prec], "data": "synthetic",
         "config": {"workload": f"tfim-{inst.n_qubits}q-N{N}-M{M}-grid{K}-tf{inst.t_f:g}ns",
                    "N": N, "M": M, "n_grid": K, "t_f_ns": inst.t_f, "precision": args.precision,
                    "tables": "FP64 eigensystems, rates, jump tables; rotation tables in the state precision",
-                   "l2": f"rotation tables {((K - 1) * N * N * (4 if prec else 8)) / 1e9:.2f} GB > L2, read once per step",
+                   "l2": f"rotation tables {((K - 1) * N * N * (8 if prec == A.AQT_PREC_FP64 else 4)) / 1e9:.2f} GB"
+                         " > L2, streamed once per run",
                    "parallelism": f"trajectories x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck,
         "table_build_s": table_s, "status": A.STATUS_NAMES.get(status, status),

@@ -59,7 +59,10 @@ typedef enum {
  * channel draw and the tables are always FP64). */
 typedef enum {
     AQT_PREC_FP64 = 0,      /* SIMT FP64 state and rotation */
-    AQT_PREC_FP32 = 1       /* SIMT FP32 state and rotation, FP64 norm sums */
+    AQT_PREC_FP32 = 1,      /* SIMT FP32 state and rotation, FP64 norm sums */
+    AQT_PREC_F16SPLIT = 2   /* tensor cores (tcgen05): rotation as O_hi C_hi + O_hi C_lo + O_lo C_hi
+                               in FP16 with FP32 accumulation (22-bit mantissa), FP32 state;
+                               needs N a multiple of 128 (n_qubits >= 7) */
 } aqt_precision;
 
 /* One jump. t is the jump time in ns; the jump happened while the generator

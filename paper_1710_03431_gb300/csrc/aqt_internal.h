@@ -77,7 +77,8 @@ struct DevTables {
     const float *ehalf32;
     const int32_t *mfirst, *msize;
     const GridMeta *meta;
-    const void *OT;  // FP64 or FP32, per precision
+    const void *OT;     // FP64 or FP32 [g][b][a]; FP16 hi/lo K-block tiles for the tensor-core path
+    const void *tclvl;  // tensor-core path: float4 [g][N] = (Re, Im of exp(-i K tau), 1 - d2, d2)
 };
 
 struct RunParams {
@@ -111,6 +112,9 @@ aqt_status set_error(aqt_ctx *ctx, aqt_status st, const std::string &msg);
 int run_precision(const aqt_ctx *ctx);
 size_t run_smem(const aqt_ctx *ctx);
 size_t simt_smem_bytes(int N, int TT, int precision);
+size_t tc_smem_bytes(int N, int TT);
+int tc_shape(int N, int64_t M, int num_sms);
+int launch_tc(const RunParams &p, void *stream, size_t smem);
 void simt_shape(int N, int64_t M, int precision, int num_sms, int *TT, int *RA);
 
 }  // namespace aqt

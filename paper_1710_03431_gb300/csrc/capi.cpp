@@ -1,4 +1,5 @@
 // C ABI of the AME trajectory library (declarations and contracts in include/aqt.h).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,7 +14,7 @@
 using namespace aqt;
 
 struct Layout {
-    size_t kdiag, ehalf, ehalf32, d2, G, M, lvlE, mfirst, msize, meta, OT;
+    size_t kdiag, ehalf, ehalf32, d2, G, M, lvlE, mfirst, msize, meta, OT, tclvl;
     size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, total;
 };
 
@@ -62,10 +63,17 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 void compute_layout(aqt_ctx *c) {
     const Inputs &in = c->in;
     const size_t n = in.n, N = (size_t)1 << in.n, K = in.K;
-    const size_t rs = in.precision == AQT_PREC_FP64 ? 8 : 4;
-    simt_shape((int)N, in.M, in.precision, c->num_sms, &c->TT, &c->RA);
+    const bool tc = in.precision == AQT_PREC_F16SPLIT;
+    const size_t rs = in.precision == AQT_PREC_FP64 ? 8 : tc ? 4 : 4;
+    if (tc) {
+        c->TT = tc_shape((int)N, in.M, c->num_sms);
+        c->RA = 0;
+        c->smem = tc_smem_bytes((int)N, c->TT);
+    } else {
+        simt_shape((int)N, in.M, in.precision, c->num_sms, &c->TT, &c->RA);
+        c->smem = simt_smem_bytes((int)N, c->TT, in.precision);
+    }
     c->n_cta = (int)((in.M + c->TT - 1) / c->TT);
-    c->smem = simt_smem_bytes((int)N, c->TT, in.precision);
     Layout &L = c->lay;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -83,7 +91,8 @@ void compute_layout(aqt_ctx *c) {
     L.mfirst = take(K * N * 4);
     L.msize = take(K * N * 4);
     L.meta = take(K * sizeof(GridMeta));
-    L.OT = take((K - 1) * N * N * rs);
+    L.OT = take((K - 1) * N * N * rs);  // FP16 hi + lo for the tensor-core path: also 4 bytes per entry
+    L.tclvl = take(tc ? K * N * 16 : 0);
     L.final_state = take((size_t)in.M * N * 2 * 8);
     L.jumps = take((size_t)std::max<int64_t>(in.jcap, 1) * sizeof(aqt_jump));
     L.jcount = take(8);
@@ -154,6 +163,7 @@ aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
     p->tab.msize = (const int32_t *)(c->ws + L.msize);
     p->tab.meta = (const GridMeta *)(c->ws + L.meta);
     p->tab.OT = c->ws + L.OT;
+    p->tab.tclvl = c->ws + L.tclvl;
     return AQT_OK;
 }
 
@@ -253,7 +263,7 @@ aqt_status aqt_set_grid(aqt_ctx *c, double t_f, int n_grid) {
 aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precision, int64_t jump_capacity) {
     if (!c) return AQT_EINVAL;
     if (M < 1 || M > (int64_t)1 << 31) return fail(c, AQT_EINVAL, "M must be in [1, 2^31]");
-    if (precision != AQT_PREC_FP64 && precision != AQT_PREC_FP32)
+    if (precision != AQT_PREC_FP64 && precision != AQT_PREC_FP32 && precision != AQT_PREC_F16SPLIT)
         return fail(c, AQT_EINVAL, "unknown precision");
     if (jump_capacity < 0) return fail(c, AQT_EINVAL, "jump_capacity must be >= 0");
     c->in.M = M;
@@ -268,6 +278,8 @@ aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precis
 aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set ising, schedule, bath, grid and trajectories first");
+    if (c->in.precision == AQT_PREC_F16SPLIT && c->in.n < 7)
+        return fail(c, AQT_EINVAL, "the tensor-core path needs N a multiple of 128 (n_qubits >= 7)");
     compute_layout(c);
     *bytes = c->lay.total;
     return AQT_OK;
@@ -323,6 +335,38 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     if (c->in.precision == AQT_PREC_FP64) {
         if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
         if (!e) e = cudaStreamSynchronize(st);
+    } else if (c->in.precision == AQT_PREC_F16SPLIT) {
+        // A-operand tiles: per grid step and K-block of 16 levels b, the hi then
+        // lo halves of O[a][b] in 8x16-byte core matrices, core (a/8, k/8) at
+        // ((a/8)*2 + k/8)*128 bytes, row a%8 at 16 bytes, column k%8 at 2 bytes.
+        const size_t N = t.N, NK = N / 16, K = t.K;
+        std::vector<__half> o16((K - 1) * N * N * 2);
+        for (size_t g = 0; g + 1 < K; ++g)
+            for (size_t kb = 0; kb < NK; ++kb) {
+                __half *hi = &o16[((g * NK + kb) * 2) * N * 16];
+                __half *lo = hi + N * 16;
+                for (size_t a = 0; a < N; ++a)
+                    for (size_t k = 0; k < 16; ++k) {
+                        const double o = t.OT[g * N * N + (kb * 16 + k) * N + a];
+                        const __half h = __float2half_rn((float)o);
+                        const __half l = __float2half_rn((float)(o - (double)__half2float(h)));
+                        const size_t off = ((a >> 3) * 2 + (k >> 3)) * 64 + (a & 7) * 8 + (k & 7);
+                        hi[off] = h;
+                        lo[off] = l;
+                    }
+            }
+        std::vector<float> lv(K * N * 4);
+        for (size_t g = 0; g < K; ++g)
+            for (size_t a = 0; a < N; ++a) {
+                const double im = t.kdiag[(g * N + a) * 2 + 1];
+                lv[(g * N + a) * 4 + 0] = (float)t.ehalf[(g * N + a) * 2];
+                lv[(g * N + a) * 4 + 1] = (float)t.ehalf[(g * N + a) * 2 + 1];
+                lv[(g * N + a) * 4 + 2] = (float)(-std::expm1(2.0 * im * t.tau));
+                lv[(g * N + a) * 4 + 3] = (float)t.d2[g * N + a];
+            }
+        if (!e) e = put(L.OT, o16.data(), o16.size() * sizeof(__half));
+        if (!e) e = put(L.tclvl, lv.data(), lv.size() * 4);
+        if (!e) e = cudaStreamSynchronize(st);
     } else {
         std::vector<float> o32(t.OT.begin(), t.OT.end());
         if (!e) e = put(L.OT, o32.data(), o32.size() * 4);
@@ -369,6 +413,7 @@ aqt_status aqt_run(aqt_ctx *c, void *stream) {
     p.tab.msize = (const int32_t *)(c->ws + L.msize);
     p.tab.meta = (const GridMeta *)(c->ws + L.meta);
     p.tab.OT = c->ws + L.OT;
+    p.tab.tclvl = c->ws + L.tclvl;
     p.final_state = (double *)(c->ws + L.final_state);
     p.jumps = (aqt_jump *)(c->ws + L.jumps);
     p.jcap = in.jcap;

@@ -1,0 +1,633 @@
+// Tensor-core propagation of AME quantum-jump trajectories (sm_103a, tcgen05).
+//
+// Same path as the SIMT kernel (arXiv:1710.03431, Sec. IV; eigenframe split of
+// H_eff, Eq. Heff), for N a multiple of 128 levels. Per grid step g-1 -> g the
+// frame rotation c <- O_{g-1} c of all TT trajectories of a CTA is one
+// tensor-core product D[level][column] = O[level][b] C[b][column], columns =
+// (trajectory, re/im) pairs, in split-FP16 form with FP32 accumulation:
+//   O C ~ O_hi C_hi + O_hi C_lo + O_lo C_hi   (hi = fp16(x), lo = fp16(x - hi)),
+// a 22-bit-mantissa product. Roles (one CTA per SM, persistent over the grid):
+//   warp 0  streams O_hi/O_lo K-blocks (16 levels) into a 4-stage shared-memory
+//           ring with bulk copies (cp.async.bulk, mbarrier transaction counts);
+//   warp 1  owns the tensor memory and issues tcgen05.mma from one lane;
+//   warps 2-9 are the epilogue: read D from tensor memory, form per-trajectory
+//           norms and decay sums (cross-lane reductions), take both frozen
+//           half-steps around s_g with the exact diagonal factors, test the
+//           norm-threshold jump clock in FP64, accumulate the observable, and
+//           write the next step's C_hi/C_lo operand back into shared memory.
+// Trajectories whose clock crosses its threshold are handed, in FP64, to the
+// same jump resolution as the SIMT kernel (App. C; App. B.1, Eq. Pi(t);
+// Eq. jump), one epilogue warp per trajectory.
+//
+// Operand layouts (no swizzle, 8x16-byte core matrices):
+//   A = O block [N rows][16 cols], K-major: core (r/8, k/8) at ((r/8)*2 + k/8)*128 B
+//       (K-core stride 128 B, M-core stride 256 B); hi then lo (N*32 B each).
+//   B = C [N levels][NC cols], MN-major: core (b/8, n/8) at ((b/8)*(NC/8) + n/8)*128 B
+//       (N-core stride 128 B, K-core stride NC*16 B).
+// Every wait on an mbarrier is bounded; on expiry the kernel records
+// kStatusTimeout, stops issuing work, and still frees its tensor memory.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "aqt_internal.h"
+#include "device_jump.cuh"
+#include "philox.cuh"
+
+namespace aqt {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kTcThreads = 320;
+constexpr int kEpiThreads = 256;
+constexpr int kStages = 4;
+constexpr int kSlots = 8;
+constexpr long long kWaitLimit = 1ll << 22;  // far above any legitimate wait (~100 us)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the abort flag set) when the limit expires.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *status) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicOr(status, kStatusTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float v[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Split x into (hi, lo) halves.
+__device__ __forceinline__ void split_half(float x, __half &hi, __half &lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
+struct TcShared {
+    // per-trajectory state (TT entries each), carved from dynamic smem
+    double *ell, *logr, *x;
+    float *scale, *P;
+    int *nj, *flag, *list;
+    float *red;  // [4][NC/8][16]
+    double *obs;
+    int *count;
+    volatile int *abort_flag;
+    int *epi_ok;  // the epilogue's go/stop decision for the current step, one writer
+    uint32_t *tmem_base;
+    uint64_t *bars;  // full[4], empty[4], dfull, bready
+};
+
+// Epilogue threads write the rows of B (levels a of this thread) for one
+// chunk of 8 columns: (re, im) of 4 trajectories as FP16 hi/lo.
+__device__ __forceinline__ void store_chunk(unsigned char *sB_hi, unsigned char *sB_lo, int NC, int a, int c,
+                                            const float v[8]) {
+    __half h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) split_half(v[i], h[i], l[i]);
+    const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
+    uint4 ph, pl;
+    ph.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+    ph.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+    ph.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
+    ph.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
+    pl.x = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
+    pl.y = (uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16);
+    pl.z = (uint32_t)__half_as_ushort(l[4]) | ((uint32_t)__half_as_ushort(l[5]) << 16);
+    pl.w = (uint32_t)__half_as_ushort(l[6]) | ((uint32_t)__half_as_ushort(l[7]) << 16);
+    *reinterpret_cast<uint4 *>(sB_hi + off) = ph;
+    *reinterpret_cast<uint4 *>(sB_lo + off) = pl;
+}
+
+// Write one trajectory's (re, im) at level a into B (2 of the 8 halves of a row chunk).
+__device__ __forceinline__ void store_one(unsigned char *sB_hi, unsigned char *sB_lo, int NC, int a, int t,
+                                          double re, double im) {
+    const int n = 2 * t;
+    const size_t off = ((size_t)(a >> 3) * (NC >> 3) + (n >> 3)) * 128 + (a & 7) * 16 + (n & 7) * 2;
+    __half h0, l0, h1, l1;
+    split_half((float)re, h0, l0);
+    split_half((float)im, h1, l1);
+    *reinterpret_cast<uint32_t *>(sB_hi + off) =
+        (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+    *reinterpret_cast<uint32_t *>(sB_lo + off) =
+        (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+}
+
+// Reduce 16 per-lane values over the warp; afterwards the even lane 2*i
+// (and its odd partner) holds the warp total of value index
+// ((lane>>4)&1)*8 + ((lane>>3)&1)*4 + ((lane>>2)&1)*2 + ((lane>>1)&1).
+__device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+    for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float send = upper ? v[i] : v[i + n / 2];
+            const float keep = upper ? v[i + n / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int scatter_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, MH = N / 128, NK = N / 16;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t b_bytes = (size_t)N * NC * 2;
+    const uint32_t stage_bytes = (uint32_t)N * 64;
+    unsigned char *sB_hi = smem;
+    unsigned char *sB_lo = smem + b_bytes;
+    unsigned char *sA = smem + 2 * b_bytes;
+    unsigned char *misc = sA + (size_t)kStages * stage_bytes;
+    TcShared S;
+    S.bars = reinterpret_cast<uint64_t *>(misc);                      // 10 barriers
+    S.tmem_base = reinterpret_cast<uint32_t *>(misc + 96);
+    S.abort_flag = reinterpret_cast<volatile int *>(misc + 100);
+    S.count = reinterpret_cast<int *>(misc + 104);
+    S.epi_ok = reinterpret_cast<int *>(misc + 108);
+    S.obs = reinterpret_cast<double *>(misc + 112);                   // [2]
+    S.ell = reinterpret_cast<double *>(misc + 128);
+    S.logr = S.ell + TT;
+    S.x = S.logr + TT;
+    S.scale = reinterpret_cast<float *>(S.x + TT);
+    S.P = S.scale + TT;
+    S.nj = reinterpret_cast<int *>(S.P + TT);
+    S.flag = S.nj + TT;
+    S.list = S.flag + TT;
+    S.red = reinterpret_cast<float *>(S.list + TT + (TT & 1));
+
+    const uint32_t bar_full = smem_u32(S.bars), bar_empty = bar_full + 8 * kStages;
+    const uint32_t bar_dfull = bar_full + 16 * kStages, bar_bready = bar_dfull + 8;
+    const int64_t t0 = (int64_t)blockIdx.x * TT;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_dfull, 1);
+        mbar_init(bar_bready, kEpiThreads);
+        *S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(MH * NC)) ncols <<= 1;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(S.tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *S.tmem_base;
+
+    if (warp == 0) {
+        // ---------------- bulk-copy producer ----------------
+        if (lane == 0) {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(p.tab.OT);
+            long long it = 0;
+            for (int g = 1; g < K && !*S.abort_flag; ++g) {
+                for (int kb = 0; kb < NK; ++kb, ++it) {
+                    const int slot = (int)(it % kStages);
+                    if (it >= kStages &&
+                        !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1), S.abort_flag, p.status))
+                        break;
+                    mbar_expect_tx(bar_full + 8 * slot, stage_bytes);
+                    bulk_g2s(smem_u32(sA + (size_t)slot * stage_bytes),
+                             src + ((size_t)(g - 1) * NK + kb) * stage_bytes, stage_bytes, bar_full + 8 * slot);
+                }
+            }
+            // drain: wait (bounded) for the copies still in flight
+            for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
+                if (!mbar_wait(bar_full + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), S.abort_flag,
+                               p.status))
+                    break;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (0u << 7) | (0u << 10) | (0u << 15) | (1u << 16) |
+                                   ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
+            const uint32_t a_lbo = 128, a_sbo = 256;
+            const uint32_t b_lbo = (uint32_t)NC * 16, b_sbo = 128;
+            const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
+            long long it = 0;
+            uint32_t last_bar = 0, last_par = 0;
+            for (int g = 1; g < K; ++g) {
+                if (!mbar_wait(bar_bready, (uint32_t)((g - 1) & 1), S.abort_flag, p.status)) break;
+                fence_after();
+                bool ok = true;
+                for (int kb = 0; kb < NK; ++kb, ++it) {
+                    const int slot = (int)(it % kStages);
+                    if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = smem_u32(sA + (size_t)slot * stage_bytes);
+                    for (int h = 0; h < MH; ++h) {
+                        const uint32_t d = tmem + (uint32_t)(h * NC);
+                        const uint64_t ahi = umma_desc(a0 + h * 4096, a_lbo, a_sbo);
+                        const uint64_t alo = umma_desc(a0 + (uint32_t)N * 32 + h * 4096, a_lbo, a_sbo);
+                        const uint64_t bh = umma_desc(bhi + (uint32_t)kb * NC * 32, b_lbo, b_sbo);
+                        const uint64_t bl = umma_desc(blo + (uint32_t)kb * NC * 32, b_lbo, b_sbo);
+                        umma_f16(d, ahi, bh, idesc, kb > 0 ? 1u : 0u);
+                        umma_f16(d, ahi, bl, idesc, 1u);
+                        umma_f16(d, alo, bh, idesc, 1u);
+                    }
+                    umma_commit(bar_empty + 8 * slot);
+                    last_bar = bar_empty + 8 * slot;
+                    last_par = (uint32_t)((it / kStages) & 1);
+                }
+                if (!ok) break;
+                umma_commit(bar_dfull);
+            }
+            // on an abort, let the products already issued finish (bounded)
+            // before the tensor memory is released
+            if (*S.abort_flag && last_bar) {
+                for (long long i = 0; i < kWaitLimit; ++i)
+                    if (mbar_try(last_bar, last_par)) break;
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;
+        const int nchunk = NC / 8;
+        double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * 2 * N;
+        const float4 *lvl = reinterpret_cast<const float4 *>(p.tab.tclvl);
+
+        // ---- initial state e_0 and the half-step after s_0 ------------------------
+        if (etid < TT) {
+            const int t = etid;
+            const bool active = t0 + t < p.M;
+            S.nj[t] = 0;
+            S.x[t] = active ? 1.0 : 0.0;
+            if (active) {
+                S.logr[t] = log(uniform01(traj_event(p.seed, t0 + t, 0).x[0]));
+                const double l = log(p.tab.d2[0]);
+                S.ell[t] = l;
+                S.flag[t] = (l <= S.logr[t]) ? 1 : 0;
+            } else {
+                S.logr[t] = 0.0;
+                S.ell[t] = 0.0;
+                S.flag[t] = 2;
+            }
+        }
+        if (etid == 0) *S.count = 0;
+        epi_sync();
+        if (etid < TT && S.flag[etid] == 1) S.list[atomicAdd(S.count, 1)] = etid;
+        // B rows for all levels: level 0 holds exp(-i K_00 tau)/|.| for non-crossed
+        {
+            const double er = p.tab.ehalf[0], ei = p.tab.ehalf[1];
+            const double nrm = sqrt(er * er + ei * ei);
+            for (int h = 0; h < MH; ++h) {
+                const int a = 128 * h + 32 * q + lane;
+                for (int c = ch; c < nchunk; c += 2) {
+                    float v[8];
+                    for (int j = 0; j < 4; ++j) {
+                        const int t = 4 * c + j;
+                        const bool keep = a == 0 && S.flag[t] == 0;
+                        v[2 * j] = keep ? (float)(er / nrm) : 0.0f;
+                        v[2 * j + 1] = keep ? (float)(ei / nrm) : 0.0f;
+                    }
+                    store_chunk(sB_hi, sB_lo, NC, a, c, v);
+                }
+            }
+        }
+        epi_sync();
+        // crossed at the first half-step: FP64 resolution from e_0
+        for (int base = 0; base < *S.count; base += kSlots) {
+            const int nr = min(kSlots, *S.count - base);
+            for (int sidx = 0; sidx < nr; ++sidx)
+                for (int h = 0; h < MH; ++h) {
+                    const int a = 128 * h + 32 * q + lane;
+                    if (ch == 0) scr[(size_t)sidx * 2 * N + a] = make_double2(a == 0 ? 1.0 : 0.0, 0.0);
+                }
+            epi_sync();
+            if (e < nr) {
+                const int t = S.list[base + e];
+                double el = 0.0, lr = S.logr[t];
+                int nj = S.nj[t];
+                double2 *c64 = scr + (size_t)e * 2 * N;
+                half_step64(p, 0, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                if (lane == 0) {
+                    S.ell[t] = el;
+                    S.logr[t] = lr;
+                    S.nj[t] = nj;
+                }
+            }
+            epi_sync();
+            for (int sidx = 0; sidx < nr; ++sidx) {
+                const int t = S.list[base + sidx];
+                for (int h = 0; h < MH; ++h) {
+                    const int a = 128 * h + 32 * q + lane;
+                    if (ch == 0) {
+                        const double2 v = scr[(size_t)sidx * 2 * N + a];
+                        store_one(sB_hi, sB_lo, NC, a, t, v.x, v.y);
+                    }
+                }
+            }
+            epi_sync();
+        }
+        // observable at s_0 (every active trajectory is in the ground state)
+        if (e == 0) {
+            double sx = 0.0, sx2 = 0.0;
+            for (int t = lane; t < TT; t += 32) {
+                sx += S.x[t];
+                sx2 += S.x[t] * S.x[t];
+            }
+            sx = warp_sum(sx);
+            sx2 = warp_sum(sx2);
+            if (lane == 0) {
+                p.obs_part[((size_t)blockIdx.x * K) * 2] = sx;
+                p.obs_part[((size_t)blockIdx.x * K) * 2 + 1] = sx2;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        mbar_arrive(bar_bready);
+
+        for (int g = 1; g < K; ++g) {
+            const bool last = g == K - 1;
+            // one thread waits for the products; all epilogue threads then take
+            // the same decision (a bounded wait can expire for one thread only)
+            if (etid == 0) *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status) ? 1 : 0;
+            epi_sync();
+            if (!*S.epi_ok) break;
+            fence_after();
+            const int gs = p.tab.meta[g].gs_size;
+            float4 L[4];
+            for (int h = 0; h < MH; ++h) L[h] = lvl[(size_t)g * N + 128 * h + 32 * q + lane];
+            // ---- pass 1: per-trajectory sums over levels ------------------------------
+            for (int c = ch; c < nchunk; c += 2) {
+                float v16[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
+                for (int h = 0; h < MH; ++h) {
+                    float d[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
+                    const int a = 128 * h + 32 * q + lane;
+                    const float w = L[h].z, d2 = L[h].w;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float qv = d[2 * j] * d[2 * j] + d[2 * j + 1] * d[2 * j + 1];
+                        v16[j] += qv;
+                        v16[4 + j] += qv * w;
+                        v16[8 + j] += qv * d2 * w;
+                        if (a < gs) v16[12 + j] += qv * d2;
+                    }
+                }
+                const float tot = reduce_scatter16(v16, lane);
+                if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+            }
+            if (etid == 0) *S.count = 0;
+            epi_sync();
+            // ---- pass 2: clocks, crossings, scales, observable ---------------------------
+            if (etid < TT) {
+                const int t = etid, c = t >> 2, j = t & 3;
+                if (S.flag[t] != 2) {
+                    float Pt = 0.f, Db = 0.f, Da = 0.f, X = 0.f;
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const float *r = S.red + ((size_t)qq * nchunk + c) * 16;
+                        Pt += r[j];
+                        Db += r[4 + j];
+                        Da += r[8 + j];
+                        X += r[12 + j];
+                    }
+                    S.P[t] = Pt;
+                    const float dB = Db / Pt;
+                    const double lB = S.ell[t] + (double)log1pf(-dB);
+                    const float nB = Pt - Db;
+                    bool cross = lB <= S.logr[t];
+                    float dA = 0.f;
+                    double lA = lB;
+                    if (!cross && !last) {
+                        dA = Da / nB;
+                        lA = lB + (double)log1pf(-dA);
+                        cross = lA <= S.logr[t];
+                    }
+                    if (!(Pt > 0.f) || !isfinite(Pt)) {
+                        atomicOr(p.status, kStatusNumeric);
+                        cross = false;
+                    }
+                    if (!cross) {
+                        S.flag[t] = 0;
+                        S.ell[t] = last ? lB : lA;
+                        S.x[t] = (double)X / (double)nB;
+                        S.scale[t] = last ? rsqrtf(nB) : rsqrtf(nB) * rsqrtf(1.0f - dA);
+                    } else {
+                        S.flag[t] = 1;
+                        S.list[atomicAdd(S.count, 1)] = t;
+                    }
+                }
+            }
+            epi_sync();
+            // ---- pass 3: next state (or final state) for non-crossed trajectories ----------
+            for (int c = ch; c < nchunk; c += 2) {
+                for (int h = 0; h < MH; ++h) {
+                    float d[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
+                    const int a = 128 * h + 32 * q + lane;
+                    // exp(-i K tau) squared: both half-steps at s_g
+                    const float er = L[h].x, ei = L[h].y;
+                    const float e2r = last ? er : er * er - ei * ei, e2i = last ? ei : 2.f * er * ei;
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int t = 4 * c + j;
+                        const float s = S.flag[t] == 0 ? S.scale[t] : 0.f;
+                        const float re = d[2 * j], im = d[2 * j + 1];
+                        v[2 * j] = (re * e2r - im * e2i) * s;
+                        v[2 * j + 1] = (re * e2i + im * e2r) * s;
+                    }
+                    if (!last) {
+                        store_chunk(sB_hi, sB_lo, NC, a, c, v);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int t = 4 * c + j;
+                            if (S.flag[t] == 0) {
+                                double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
+                                fs[0] = v[2 * j];
+                                fs[1] = v[2 * j + 1];
+                            }
+                        }
+                    }
+                }
+            }
+            // ---- crossed trajectories: FP64 resolution of both half-steps ---------------------
+            const int ncross = *S.count;
+            for (int base = 0; base < ncross; base += kSlots) {
+                const int nr = min(kSlots, ncross - base);
+                if (ch == 0) {
+                    for (int sidx = 0; sidx < nr; ++sidx) {
+                        const int t = S.list[base + sidx];
+                        const double inv = 1.0 / sqrt((double)S.P[t]);
+                        const int c = t >> 2, j = t & 3;
+                        for (int h = 0; h < MH; ++h) {
+                            const int a = 128 * h + 32 * q + lane;
+                            float d[8];
+                            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
+                            scr[(size_t)sidx * 2 * N + a] = make_double2(d[2 * j] * inv, d[2 * j + 1] * inv);
+                        }
+                    }
+                }
+                epi_sync();
+                if (e < nr) {
+                    const int t = S.list[base + e];
+                    double el = S.ell[t], lr = S.logr[t];
+                    int nj = S.nj[t];
+                    double2 *c64 = scr + (size_t)e * 2 * N;
+                    half_step64(p, g, 0, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    double xs = 0.0;
+                    for (int a = lane; a < gs; a += 32) xs += c64[a].x * c64[a].x + c64[a].y * c64[a].y;
+                    xs = warp_sum(xs);
+                    if (!last) half_step64(p, g, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    if (lane == 0) {
+                        S.ell[t] = el;
+                        S.logr[t] = lr;
+                        S.nj[t] = nj;
+                        S.x[t] = xs;
+                    }
+                }
+                epi_sync();
+                for (int sidx = 0; sidx < nr && ch == 0; ++sidx) {
+                    const int t = S.list[base + sidx];
+                    for (int h = 0; h < MH; ++h) {
+                        const int a = 128 * h + 32 * q + lane;
+                        const double2 v = scr[(size_t)sidx * 2 * N + a];
+                        if (!last) {
+                            store_one(sB_hi, sB_lo, NC, a, t, v.x, v.y);
+                        } else {
+                            double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
+                            fs[0] = v.x;
+                            fs[1] = v.y;
+                        }
+                    }
+                }
+                epi_sync();
+            }
+            // ---- observable partials (fixed order) -----------------------------------------
+            if (e == 0) {
+                double sx = 0.0, sx2 = 0.0;
+                for (int t = lane; t < TT; t += 32) {
+                    if (S.flag[t] == 2) continue;
+                    sx += S.x[t];
+                    sx2 += S.x[t] * S.x[t];
+                }
+                sx = warp_sum(sx);
+                sx2 = warp_sum(sx2);
+                if (lane == 0) {
+                    p.obs_part[((size_t)blockIdx.x * K + g) * 2] = sx;
+                    p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = sx2;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
+            mbar_arrive(bar_bready);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int N, int TT) {
+    const int NC = 2 * TT;
+    size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
+    b += 128 + (size_t)TT * (8 * 3 + 4 * 2 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
+    b = (b + 1023) & ~(size_t)1023;
+    // one CTA per SM: the kernel allocates tensor-memory columns without sharing
+    return b < 120 * 1024 ? 120 * 1024 : b;
+}
+
+// Trajectories per CTA: a multiple of 8 (columns in chunks of 16) so that the
+// grid fills the SMs once, within shared memory and 256 tensor-core columns.
+int tc_shape(int N, int64_t M, int num_sms) {
+    int tt = (int)((M + num_sms - 1) / num_sms);
+    tt = (tt + 7) & ~7;
+    if (tt < 8) tt = 8;
+    while (tt > 8 && (tc_smem_bytes(N, tt) > 227 * 1024 || 2 * tt * (N / 128) > 512 || 2 * tt > 256)) tt -= 8;
+    return tt;
+}
+
+int launch_tc(const RunParams &p, void *stream, size_t smem) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(propagate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    propagate_tc<<<p.n_cta, kTcThreads, smem, st>>>(p);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace aqt

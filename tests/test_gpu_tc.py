@@ -1,0 +1,75 @@
+"""Tensor-core (tcgen05, split-FP16) path against the FP64 oracle and the FP64
+GPU path, through the C ABI.
+
+The rotation runs as O_hi C_hi + O_hi C_lo + O_lo C_hi with FP32 accumulation
+(22-bit mantissa), the state is FP32 and the jump clock, crossing time and
+channel draw are FP64. With common random numbers almost every trajectory
+keeps the oracle's jump sequence; the rare ones whose channel draw sits within
+the rounding error of a CDF boundary may diverge, so parity is asserted on the
+identical ones and statistically on all.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ame
+from test_gpu_parity import compare_crn, run_lib, se_bound
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,M,grid,eta", [(7, 40, 101, 0.02), (8, 24, 41, 0.01)])
+def test_tc_against_oracle(aqt_lib, n, M, grid, eta):
+    """N = 128 and 256; ragged M (not a multiple of the 8-trajectory tile)."""
+    inst = W.tfim_instance(n, 100 + n, eta_g2=eta, t_f=5.0, n_grid=grid, seed=21)
+    res = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_F16SPLIT, M=M)
+    assert res["status"] == aqt_lib.AQT_OK
+    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-5, state_tol=2e-5, min_identical=0.9)
+    assert len(oj) > 0
+    assert np.max(np.abs(res["s1"] - p.sum(axis=0))) < 2e-4 * M
+
+
+def test_tc_matches_fp64_gpu(aqt_lib):
+    """Same instance, same streams: split-FP16 tensor-core run vs FP64 SIMT run."""
+    inst = W.tfim_instance(7, 207, eta_g2=0.02, t_f=8.0, n_grid=301, seed=5)
+    M = 300
+    r64 = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_FP64, M=M)
+    rtc = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_F16SPLIT, M=M)
+    assert rtc["status"] == aqt_lib.AQT_OK
+    j64 = {}
+    for r in r64["jumps"]:
+        j64.setdefault(int(r["traj"]), []).append((r["grid"], r["half"], r["alpha"], r["src"], r["dst"]))
+    jtc = {}
+    for r in rtc["jumps"]:
+        jtc.setdefault(int(r["traj"]), []).append((r["grid"], r["half"], r["alpha"], r["src"], r["dst"]))
+    same = [t for t in range(M) if j64.get(t, []) == jtc.get(t, [])]
+    assert len(same) >= 0.95 * M
+    ov = np.abs(np.einsum("mi,mi->m", r64["final"][same].conj(), rtc["final"][same]))
+    assert np.max(np.abs(ov - 1.0)) < 2e-5
+    assert np.max(np.abs(rtc["s1"] - r64["s1"])) < 1e-3 * M
+
+
+def test_tc_against_ame(aqt_lib):
+    inst = W.tfim_instance(7, 307, eta_g2=0.03, t_f=6.0, n_grid=151, seed=8)
+    M = 1200
+    res = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_F16SPLIT, M=M)
+    ref = ame.run(inst)["p_gs"]
+    for k in (50, 100, 150):
+        assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], se_bound(ref[k], M)), (k, res["mean"][k], ref[k])
+
+
+def test_tc_rejects_small_n(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(6, 3, n_grid=5)
+    c = A.aqt_create(0)
+    A.aqt_set_ising(c, inst.n_qubits, inst.hz, inst.J)
+    A.aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
+    A.aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
+    A.aqt_set_grid(c, inst.t_f, inst.n_grid)
+    A.aqt_set_trajectories(c, 10, 1, A.AQT_PREC_F16SPLIT, 16)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_workspace_size(c)
+    assert e.value.status == A.AQT_EINVAL
+    A.aqt_destroy(c)
