@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--cpu-sample-traj", type=int, default=400)
+    ap.add_argument("--cpu-sample-traj", type=int, default=2000)
     return ap.parse_args()
 
 
