@@ -62,7 +62,7 @@ typedef enum {
     AQT_PREC_FP32 = 1,      /* SIMT FP32 state and rotation, FP64 norm sums */
     AQT_PREC_F16SPLIT = 2   /* tensor cores (tcgen05): rotation as O_hi C_hi + O_hi C_lo + O_lo C_hi
                                in FP16 with FP32 accumulation (22-bit mantissa), FP32 state;
-                               needs N a multiple of 128 (n_qubits >= 7) */
+                               N = 128 or 256 (n_qubits 7 or 8) */
 } aqt_precision;
 
 /* One jump. t is the jump time in ns; the jump happened while the generator

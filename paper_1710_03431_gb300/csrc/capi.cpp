@@ -278,8 +278,8 @@ aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precis
 aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set ising, schedule, bath, grid and trajectories first");
-    if (c->in.precision == AQT_PREC_F16SPLIT && c->in.n < 7)
-        return fail(c, AQT_EINVAL, "the tensor-core path needs N a multiple of 128 (n_qubits >= 7)");
+    if (c->in.precision == AQT_PREC_F16SPLIT && (c->in.n < 7 || c->in.n > 8))
+        return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
     compute_layout(c);
     *bytes = c->lay.total;
     return AQT_OK;

@@ -10,7 +10,7 @@
 //   warp 0  streams O_hi/O_lo K-blocks (16 levels) into a 4-stage shared-memory
 //           ring with bulk copies (cp.async.bulk, mbarrier transaction counts);
 //   warp 1  owns the tensor memory and issues tcgen05.mma from one lane;
-//   warps 2-9 are the epilogue: read D from tensor memory, form per-trajectory
+//   warps 2-13 are the epilogue (3 column groups x 4 TMEM lane quarters): read D from tensor memory, form per-trajectory
 //           norms and decay sums (cross-lane reductions), take both frozen
 //           half-steps around s_g with the exact diagonal factors, test the
 //           norm-threshold jump clock in FP64, accumulate the observable, and
@@ -42,8 +42,9 @@ namespace {
 
 using namespace dev;
 
-constexpr int kTcThreads = 320;
-constexpr int kEpiThreads = 256;
+constexpr int kEpiWarps = 12;                       // 3 column groups x 4 TMEM lane quarters
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kTcThreads = 64 + kEpiThreads;
 constexpr int kStages = 4;
 constexpr int kSlots = 8;
 constexpr long long kWaitLimit = 1ll << 22;  // far above any legitimate wait (~100 us)
@@ -106,19 +107,36 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                  : "memory");
 }
 
+
+// Issue a 32-lane x 8-column TMEM load without waiting (tcgen05.wait::ld and
+// reg_fence must follow before the values are used).
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t addr, uint32_t r[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Keep uses of loaded registers after the wait (a data dependency on an asm
+// that is ordered after tcgen05.wait::ld).
+__device__ __forceinline__ void reg_fence(uint32_t r[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) asm volatile("" : "+r"(r[i]));
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, float v[8]) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(addr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    reg_fence(r);
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // Split x into (hi, lo) halves.
 __device__ __forceinline__ void split_half(float x, __half &hi, __half &lo) {
@@ -129,7 +147,7 @@ __device__ __forceinline__ void split_half(float x, __half &hi, __half &lo) {
 struct TcShared {
     // per-trajectory state (TT entries each), carved from dynamic smem
     double *ell, *logr, *x;
-    float *scale, *P;
+    float *kinv, *P, *fscale;  // 1/kappa of the stored operand, raw |D|^2, final-state scale
     int *nj, *flag, *list;
     float *red;  // [4][NC/8][16]
     double *obs;
@@ -142,21 +160,22 @@ struct TcShared {
 
 // Epilogue threads write the rows of B (levels a of this thread) for one
 // chunk of 8 columns: (re, im) of 4 trajectories as FP16 hi/lo.
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ void store_chunk(unsigned char *sB_hi, unsigned char *sB_lo, int NC, int a, int c,
                                             const float v[8]) {
-    __half h[8], l[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) split_half(v[i], h[i], l[i]);
-    const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
     uint4 ph, pl;
-    ph.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-    ph.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
-    ph.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
-    ph.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
-    pl.x = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
-    pl.y = (uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16);
-    pl.z = (uint32_t)__half_as_ushort(l[4]) | ((uint32_t)__half_as_ushort(l[5]) << 16);
-    pl.w = (uint32_t)__half_as_ushort(l[6]) | ((uint32_t)__half_as_ushort(l[7]) << 16);
+    split2(v[0], v[1], ph.x, pl.x);
+    split2(v[2], v[3], ph.y, pl.y);
+    split2(v[4], v[5], ph.z, pl.z);
+    split2(v[6], v[7], ph.w, pl.w);
+    const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
     *reinterpret_cast<uint4 *>(sB_hi + off) = ph;
     *reinterpret_cast<uint4 *>(sB_lo + off) = pl;
 }
@@ -196,9 +215,10 @@ __device__ __forceinline__ int scatter_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
+template <int MH>  // 128-level blocks of the state (N = 128 MH)
 __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, MH = N / 128, NK = N / 16;
+    const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t b_bytes = (size_t)N * NC * 2;
     const uint32_t stage_bytes = (uint32_t)N * 64;
@@ -216,9 +236,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.ell = reinterpret_cast<double *>(misc + 128);
     S.logr = S.ell + TT;
     S.x = S.logr + TT;
-    S.scale = reinterpret_cast<float *>(S.x + TT);
-    S.P = S.scale + TT;
-    S.nj = reinterpret_cast<int *>(S.P + TT);
+    S.kinv = reinterpret_cast<float *>(S.x + TT);
+    S.P = S.kinv + TT;
+    S.fscale = S.P + TT;
+    S.nj = reinterpret_cast<int *>(S.fscale + TT);
     S.flag = S.nj + TT;
     S.list = S.flag + TT;
     S.red = reinterpret_cast<float *>(S.list + TT + (TT & 1));
@@ -319,8 +340,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
-        const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;
+        const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;  // ch: column group 0..2
         const int nchunk = NC / 8;
+        const int c_begin = (ch * nchunk) / 3, c_end = ((ch + 1) * nchunk) / 3;
         double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * 2 * N;
         const float4 *lvl = reinterpret_cast<const float4 *>(p.tab.tclvl);
 
@@ -329,6 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const int t = etid;
             const bool active = t0 + t < p.M;
             S.nj[t] = 0;
+            S.kinv[t] = 1.0f;
             S.x[t] = active ? 1.0 : 0.0;
             if (active) {
                 S.logr[t] = log(uniform01(traj_event(p.seed, t0 + t, 0).x[0]));
@@ -350,7 +373,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const double nrm = sqrt(er * er + ei * ei);
             for (int h = 0; h < MH; ++h) {
                 const int a = 128 * h + 32 * q + lane;
-                for (int c = ch; c < nchunk; c += 2) {
+                for (int c = c_begin; c < c_end; ++c) {
                     float v[8];
                     for (int j = 0; j < 4; ++j) {
                         const int t = 4 * c + j;
@@ -415,6 +438,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         fence_before();
         mbar_arrive(bar_bready);
 
+        // per-level factors of the next grid point, loaded one step ahead
+        float4 Lnext[MH];
+        int gs_next = 1;
+        if (K > 1) {
+#pragma unroll
+            for (int h = 0; h < MH; ++h) Lnext[h] = lvl[(size_t)1 * N + 128 * h + 32 * q + lane];
+            gs_next = p.tab.meta[1].gs_size;
+        }
         for (int g = 1; g < K; ++g) {
             const bool last = g == K - 1;
             // one thread waits for the products; all epilogue threads then take
@@ -423,49 +454,101 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             epi_sync();
             if (!*S.epi_ok) break;
             fence_after();
-            const int gs = p.tab.meta[g].gs_size;
-            float4 L[4];
-            for (int h = 0; h < MH; ++h) L[h] = lvl[(size_t)g * N + 128 * h + 32 * q + lane];
-            // ---- pass 1: per-trajectory sums over levels ------------------------------
-            for (int c = ch; c < nchunk; c += 2) {
+            const int gs = gs_next;
+            float4 L[MH];
+#pragma unroll
+            for (int h = 0; h < MH; ++h) L[h] = Lnext[h];
+            if (g + 1 < K) {
+#pragma unroll
+                for (int h = 0; h < MH; ++h) Lnext[h] = lvl[(size_t)(g + 1) * N + 128 * h + 32 * q + lane];
+                gs_next = p.tab.meta[g + 1].gs_size;
+            }
+            // exp(-i K tau) squared: both half-steps at s_g (one at the last grid point)
+            float e2r[MH], e2i[MH];
+#pragma unroll
+            for (int h = 0; h < MH; ++h) {
+                e2r[h] = last ? L[h].x : L[h].x * L[h].x - L[h].y * L[h].y;
+                e2i[h] = last ? L[h].y : 2.f * L[h].x * L[h].y;
+            }
+            // ---- single pass: per-trajectory sums over levels, and the next operand ----
+            // D = kappa_{g-1} O c_{g-1}; the operand written now is D E^2 / kappa_{g-1}
+            // = (O c) E^2, whose norm is restored to 1 through kappa_g next step.
+            // one chunk of 8 columns: sums and the operand rows of this thread's levels
+            auto process = [&](int c, uint32_t (&r)[MH][8]) {
                 float v16[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
+                float ki[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
+#pragma unroll
                 for (int h = 0; h < MH; ++h) {
-                    float d[8];
-                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
                     const int a = 128 * h + 32 * q + lane;
-                    const float w = L[h].z, d2 = L[h].w;
+                    const float w = L[h].z, d2 = L[h].w, d2w = d2 * w;
+                    const bool in_gs = a < gs;
+                    float v[8];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float qv = d[2 * j] * d[2 * j] + d[2 * j + 1] * d[2 * j + 1];
+                        const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
+                        const float qv = fmaf(re, re, im * im);
                         v16[j] += qv;
-                        v16[4 + j] += qv * w;
-                        v16[8 + j] += qv * d2 * w;
-                        if (a < gs) v16[12 + j] += qv * d2;
+                        v16[4 + j] = fmaf(qv, w, v16[4 + j]);
+                        v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
+                        if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
+                        const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
+                        v[2 * j] = fmaf(re, fr, -im * fi);
+                        v[2 * j + 1] = fmaf(re, fi, im * fr);
                     }
+                    if (!last) store_chunk(sB_hi, sB_lo, NC, a, c, v);
                 }
                 const float tot = reduce_scatter16(v16, lane);
                 if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+            };
+            auto issue = [&](int c, uint32_t (&r)[MH][8]) {
+#pragma unroll
+                for (int h = 0; h < MH; ++h)
+                    tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r[h]);
+            };
+            auto settle = [&](uint32_t (&r)[MH][8]) {
+                tmem_wait();
+#pragma unroll
+                for (int h = 0; h < MH; ++h) reg_fence(r[h]);
+            };
+            // the loads of chunk c+1 are in flight while chunk c is processed
+            {
+                uint32_t rA[MH][8], rB[MH][8];
+                int c = c_begin;
+                if (c < c_end) issue(c, rA);
+                settle(rA);
+                while (c < c_end) {
+                    if (c + 1 < c_end) issue(c + 1, rB);
+                    process(c, rA);
+                    settle(rB);
+                    if (++c >= c_end) break;
+                    if (c + 1 < c_end) issue(c + 1, rA);
+                    process(c, rB);
+                    settle(rA);
+                    ++c;
+                }
             }
             if (etid == 0) *S.count = 0;
             epi_sync();
-            // ---- pass 2: clocks, crossings, scales, observable ---------------------------
+            // ---- per trajectory: clock, crossings, next kappa, observable -------------------
             if (etid < TT) {
                 const int t = etid, c = t >> 2, j = t & 3;
                 if (S.flag[t] != 2) {
                     float Pt = 0.f, Db = 0.f, Da = 0.f, X = 0.f;
                     for (int qq = 0; qq < 4; ++qq) {
-                        const float *r = S.red + ((size_t)qq * nchunk + c) * 16;
-                        Pt += r[j];
-                        Db += r[4 + j];
-                        Da += r[8 + j];
-                        X += r[12 + j];
+                        const float *rr = S.red + ((size_t)qq * nchunk + c) * 16;
+                        Pt += rr[j];
+                        Db += rr[4 + j];
+                        Da += rr[8 + j];
+                        X += rr[12 + j];
                     }
                     S.P[t] = Pt;
+                    const float nB = Pt - Db;
                     const float dB = Db / Pt;
                     const double lB = S.ell[t] + (double)log1pf(-dB);
-                    const float nB = Pt - Db;
                     bool cross = lB <= S.logr[t];
                     float dA = 0.f;
                     double lA = lB;
@@ -481,8 +564,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     if (!cross) {
                         S.flag[t] = 0;
                         S.ell[t] = last ? lB : lA;
-                        S.x[t] = (double)X / (double)nB;
-                        S.scale[t] = last ? rsqrtf(nB) : rsqrtf(nB) * rsqrtf(1.0f - dA);
+                        S.x[t] = (double)(X / nB);
+                        const float ko = S.kinv[t];
+                        // kappa_g^2 = |O c|^2 (1 - dB)(1 - dA) with |O c|^2 = P kinv_{g-1}^2
+                        S.kinv[t] = rsqrtf(Pt * ko * ko * (1.0f - dB) * (1.0f - dA));
+                        S.fscale[t] = rsqrtf(nB);
                     } else {
                         S.flag[t] = 1;
                         S.list[atomicAdd(S.count, 1)] = t;
@@ -490,38 +576,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 }
             }
             epi_sync();
-            // ---- pass 3: next state (or final state) for non-crossed trajectories ----------
-            for (int c = ch; c < nchunk; c += 2) {
-                for (int h = 0; h < MH; ++h) {
-                    float d[8];
-                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
-                    const int a = 128 * h + 32 * q + lane;
-                    // exp(-i K tau) squared: both half-steps at s_g
-                    const float er = L[h].x, ei = L[h].y;
-                    const float e2r = last ? er : er * er - ei * ei, e2i = last ? ei : 2.f * er * ei;
-                    float v[8];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int t = 4 * c + j;
-                        const float s = S.flag[t] == 0 ? S.scale[t] : 0.f;
-                        const float re = d[2 * j], im = d[2 * j + 1];
-                        v[2 * j] = (re * e2r - im * e2i) * s;
-                        v[2 * j + 1] = (re * e2i + im * e2r) * s;
-                    }
-                    if (!last) {
-                        store_chunk(sB_hi, sB_lo, NC, a, c, v);
-                    } else {
+            // ---- last grid point: normalised final states ----------------------------------------
+            if (last) {
+                for (int c = c_begin; c < c_end; ++c)
+                    for (int h = 0; h < MH; ++h) {
+                        float d[8];
+                        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
+                        const int a = 128 * h + 32 * q + lane;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int t = 4 * c + j;
-                            if (S.flag[t] == 0) {
-                                double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
-                                fs[0] = v[2 * j];
-                                fs[1] = v[2 * j + 1];
-                            }
+                            if (S.flag[t] != 0) continue;
+                            const float sc = S.fscale[t], re = d[2 * j], im = d[2 * j + 1];
+                            double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
+                            fs[0] = (re * e2r[h] - im * e2i[h]) * sc;
+                            fs[1] = (re * e2i[h] + im * e2r[h]) * sc;
                         }
                     }
-                }
             }
             // ---- crossed trajectories: FP64 resolution of both half-steps ---------------------
             const int ncross = *S.count;
@@ -556,6 +627,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         S.logr[t] = lr;
                         S.nj[t] = nj;
                         S.x[t] = xs;
+                        S.kinv[t] = 1.0f;
                     }
                 }
                 epi_sync();
@@ -606,7 +678,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
 size_t tc_smem_bytes(int N, int TT) {
     const int NC = 2 * TT;
     size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
-    b += 128 + (size_t)TT * (8 * 3 + 4 * 2 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
+    b += 128 + (size_t)TT * (8 * 3 + 4 * 3 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
     b = (b + 1023) & ~(size_t)1023;
     // one CTA per SM: the kernel allocates tensor-memory columns without sharing
     return b < 120 * 1024 ? 120 * 1024 : b;
@@ -624,9 +696,11 @@ int tc_shape(int N, int64_t M, int num_sms) {
 
 int launch_tc(const RunParams &p, void *stream, size_t smem) {
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(propagate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = p.N == 128 ? propagate_tc<1> : p.N == 256 ? propagate_tc<2> : nullptr;
+    if (!kern) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    propagate_tc<<<p.n_cta, kTcThreads, smem, st>>>(p);
+    kern<<<p.n_cta, kTcThreads, smem, st>>>(p);
     return (int)cudaGetLastError();
 }
 

@@ -45,6 +45,37 @@ void parallel_for(int count, F f) {
     for (auto &x : th) x.join();
 }
 
+// out[i*ld + j] = sum_k X[i][k] Y[j][k] for i < ni, j < nj (rows of length len,
+// row-major), in 4x4 register blocks. With sym set, X == Y and only j >= i
+// blocks are computed (the caller mirrors them).
+void gram(const double *X, const double *Y, int ni, int nj, int len, double *out, int ld, bool sym) {
+    for (int i0 = 0; i0 < ni; i0 += 4)
+        for (int j0 = sym ? (i0 / 4) * 4 : 0; j0 < nj; j0 += 4) {
+            double acc[4][4] = {};
+            const int ib = std::min(4, ni - i0), jb = std::min(4, nj - j0);
+            if (ib == 4 && jb == 4) {
+                const double *x0 = X + (size_t)i0 * len, *y0 = Y + (size_t)j0 * len;
+                for (int k = 0; k < len; ++k) {
+                    const double xa = x0[k], xb = x0[len + k], xc = x0[2 * len + k], xd = x0[3 * len + k];
+                    const double ya = y0[k], yb = y0[len + k], yc = y0[2 * len + k], yd = y0[3 * len + k];
+                    acc[0][0] += xa * ya; acc[0][1] += xa * yb; acc[0][2] += xa * yc; acc[0][3] += xa * yd;
+                    acc[1][0] += xb * ya; acc[1][1] += xb * yb; acc[1][2] += xb * yc; acc[1][3] += xb * yd;
+                    acc[2][0] += xc * ya; acc[2][1] += xc * yb; acc[2][2] += xc * yc; acc[2][3] += xc * yd;
+                    acc[3][0] += xd * ya; acc[3][1] += xd * yb; acc[3][2] += xd * yc; acc[3][3] += xd * yd;
+                }
+            } else {
+                for (int i = 0; i < ib; ++i)
+                    for (int j = 0; j < jb; ++j) {
+                        double a = 0.0;
+                        for (int k = 0; k < len; ++k) a += X[(size_t)(i0 + i) * len + k] * Y[(size_t)(j0 + j) * len + k];
+                        acc[i][j] = a;
+                    }
+            }
+            for (int i = 0; i < ib; ++i)
+                for (int j = 0; j < jb; ++j) out[(size_t)(i0 + i) * ld + j0 + j] = acc[i][j];
+        }
+}
+
 void schedule_at(const Inputs &in, double s, double *A, double *B) {
     const auto &ks = in.ks;
     size_t j = 0;
@@ -179,26 +210,29 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                 }
             }
         }
-        // VT rows are eigenvectors
-        std::vector<double> VT(NN), Y(NN);
+        // VT rows are eigenvectors. sz_alpha = 1 - 2 P_alpha with P_alpha the
+        // projector on basis states whose bit alpha is set, so
+        // M_alpha = V^T sz_alpha V = I - 2 W_alpha^T W_alpha, W_alpha = those rows of V.
+        std::vector<double> VT(NN), W((size_t)N * (N / 2)), Wt((size_t)N * N);
         for (int x = 0; x < N; ++x)
             for (int a = 0; a < N; ++a) VT[(size_t)a * N + x] = V[(size_t)x * N + a];
         double *Mg = &tab.M[(size_t)g * n * NN];
         for (int al = 0; al < n; ++al) {
-            const int8_t *za = &z[(size_t)al * N];
-            for (int a = 0; a < N; ++a)
-                for (int x = 0; x < N; ++x) Y[(size_t)a * N + x] = VT[(size_t)a * N + x] * za[x];
-            double *Ma = Mg + (size_t)al * NN;
             for (int a = 0; a < N; ++a) {
-                const double *ya = &Y[(size_t)a * N];
-                for (int b = a; b < N; ++b) {
-                    const double *vb = &VT[(size_t)b * N];
-                    double acc = 0.0;
-                    for (int x = 0; x < N; ++x) acc += ya[x] * vb[x];
-                    Ma[(size_t)a * N + b] = acc;
-                    Ma[(size_t)b * N + a] = acc;
-                }
+                const double *va = &VT[(size_t)a * N];
+                double *wa = &W[(size_t)a * (N / 2)];
+                int k = 0;
+                for (int x = 0; x < N; ++x)
+                    if ((x >> al) & 1) wa[k++] = va[x];
             }
+            gram(W.data(), W.data(), N, N, N / 2, Wt.data(), N, true);
+            double *Ma = Mg + (size_t)al * NN;
+            for (int a = 0; a < N; ++a)
+                for (int b = a; b < N; ++b) {
+                    const double v = (a == b ? 1.0 : 0.0) - 2.0 * Wt[(size_t)a * N + b];
+                    Ma[(size_t)a * N + b] = v;
+                    Ma[(size_t)b * N + a] = v;
+                }
         }
         // rates: gamma and S per level pair (a <- b), reused over alpha
         std::vector<double> gam(NN), lam(NN);
@@ -273,15 +307,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                 T0[(size_t)a * N + x] = V0[(size_t)x * N + a];
                 T1[(size_t)a * N + x] = V1[(size_t)x * N + a];
             }
-        double *OT = &tab.OT[(size_t)g * NN];
-        for (int b = 0; b < N; ++b)
-            for (int a = 0; a < N; ++a) {
-                const double *u = &T0[(size_t)b * N];
-                const double *v = &T1[(size_t)a * N];
-                double acc = 0.0;
-                for (int x = 0; x < N; ++x) acc += u[x] * v[x];
-                OT[(size_t)b * N + a] = acc;
-            }
+        gram(T0.data(), T1.data(), N, N, N, &tab.OT[(size_t)g * NN], N, false);
     });
     return AQT_OK;
 }
