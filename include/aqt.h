@@ -182,8 +182,8 @@ aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, 
                                   int32_t *status);
 
 /* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
- * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 M_alpha = V^T sz_alpha V,
- * [n][N][N]; 4 frame rotation O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1);
+ * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes
+ * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N]; 4 frame rotation O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1);
  * 5 eigenvectors V [N][N] (column a = level a); 6 manifold energy per level [N]. */
 aqt_status aqt_debug_table(aqt_ctx *ctx, int which, int grid, double *out);
 

@@ -46,7 +46,7 @@ struct Tables {
     std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
     std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
     std::vector<double> G;       // [K][n][N]  sum_a gamma(w_ab) M_alpha[a,b]^2
-    std::vector<double> M;       // [K][n][N][N] M_alpha = V^T sz_alpha V (symmetric)
+    std::vector<double> R;       // [K][n][N][N] R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b], M_alpha = V^T sz_alpha V
     std::vector<double> lvlE;    // [K][N]     energy of each level's manifold
     std::vector<int32_t> mfirst; // [K][N]     first level of each level's manifold
     std::vector<int32_t> msize;  // [K][N]     size of each level's manifold
@@ -73,7 +73,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
 
 // ------------------------------------------------------------- kernels ------
 struct DevTables {
-    const double *kdiag, *ehalf, *d2, *G, *M, *lvlE;
+    const double *kdiag, *ehalf, *d2, *G, *R, *lvlE;
     const float *ehalf32;
     const int32_t *mfirst, *msize;
     const GridMeta *meta;

@@ -14,7 +14,7 @@
 using namespace aqt;
 
 struct Layout {
-    size_t kdiag, ehalf, ehalf32, d2, G, M, lvlE, mfirst, msize, meta, OT, tclvl;
+    size_t kdiag, ehalf, ehalf32, d2, G, R, lvlE, mfirst, msize, meta, OT, tclvl;
     size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, total;
 };
 
@@ -86,7 +86,7 @@ void compute_layout(aqt_ctx *c) {
     L.ehalf32 = take(K * N * 2 * 4);
     L.d2 = take(K * N * 8);
     L.G = take(K * n * N * 8);
-    L.M = take(K * n * N * N * 8);
+    L.R = take(K * n * N * N * 8);
     L.lvlE = take(K * N * 8);
     L.mfirst = take(K * N * 4);
     L.msize = take(K * N * 4);
@@ -157,7 +157,7 @@ aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
     p->tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
     p->tab.d2 = (const double *)(c->ws + L.d2);
     p->tab.G = (const double *)(c->ws + L.G);
-    p->tab.M = (const double *)(c->ws + L.M);
+    p->tab.R = (const double *)(c->ws + L.R);
     p->tab.lvlE = (const double *)(c->ws + L.lvlE);
     p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p->tab.msize = (const int32_t *)(c->ws + L.msize);
@@ -327,7 +327,7 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     if (!e) e = put(L.ehalf32, e32.data(), e32.size() * 4);
     if (!e) e = put(L.d2, t.d2.data(), t.d2.size() * 8);
     if (!e) e = put(L.G, t.G.data(), t.G.size() * 8);
-    if (!e) e = put(L.M, t.M.data(), t.M.size() * 8);
+    if (!e) e = put(L.R, t.R.data(), t.R.size() * 8);
     if (!e) e = put(L.lvlE, t.lvlE.data(), t.lvlE.size() * 8);
     if (!e) e = put(L.mfirst, t.mfirst.data(), t.mfirst.size() * 4);
     if (!e) e = put(L.msize, t.msize.data(), t.msize.size() * 4);
@@ -407,7 +407,7 @@ aqt_status aqt_run(aqt_ctx *c, void *stream) {
     p.tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
     p.tab.d2 = (const double *)(c->ws + L.d2);
     p.tab.G = (const double *)(c->ws + L.G);
-    p.tab.M = (const double *)(c->ws + L.M);
+    p.tab.R = (const double *)(c->ws + L.R);
     p.tab.lvlE = (const double *)(c->ws + L.lvlE);
     p.tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p.tab.msize = (const int32_t *)(c->ws + L.msize);
@@ -543,7 +543,7 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
         case 0: std::copy_n(&t.evals[g * N], N, out); break;
         case 1: std::copy_n(&t.kdiag[g * N * 2], N * 2, out); break;
         case 2: std::copy_n(&t.G[g * n * N], n * N, out); break;
-        case 3: std::copy_n(&t.M[g * n * NN], n * NN, out); break;
+        case 3: std::copy_n(&t.R[g * n * NN], n * NN, out); break;
         case 4:
             for (size_t a = 0; a < N; ++a)
                 for (size_t b = 0; b < N; ++b) out[a * N + b] = t.OT[g * NN + b * N + a];

@@ -38,9 +38,17 @@ static __device__ __forceinline__ double warp_incl_scan(double v, int lane) {
     return v;
 }
 
-static __device__ __forceinline__ double gamma_ohmic(double w, double eta_g2, double omega_c, double beta) {
-    if (w == 0.0) return 2.0 * M_PI * eta_g2 / beta;
-    return 2.0 * M_PI * eta_g2 * w * exp(-fabs(w) / omega_c) / (-expm1(-beta * w));
+// Per-level factors exp(x) and (sin, cos)(x) in the precision TR: double for
+// the FP64 path; float for the FP32 and tensor-core paths, whose states are
+// FP32 (the sums, the clock and the crossing time stay FP64 either way).
+static __device__ __forceinline__ double lvl_exp(double x, double) { return exp(x); }
+static __device__ __forceinline__ double lvl_exp(double x, float) { return (double)expf((float)x); }
+static __device__ __forceinline__ void lvl_sincos(double x, double *s, double *c, double) { sincos(x, s, c); }
+static __device__ __forceinline__ void lvl_sincos(double x, double *s, double *c, float) {
+    float sf, cf;
+    sincosf((float)x, &sf, &cf);
+    *s = sf;
+    *c = cf;
 }
 
 
@@ -69,15 +77,17 @@ static __device__ int warp_pick(int N, double target, int lane, WF wfun) {
 // Resolve every jump of one trajectory inside one frozen half-step, in FP64.
 // c64 holds the normalised state at the start of the half-step; on return it
 // holds the normalised state at its end, and ell/logr/nj are updated.
+template <typename TR>
 static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t traj, double2 *c64, double2 *y64,
-                             double &ell, double &logr, int &nj, int lane) {
+                                   double &ell, double &logr, int &nj, int lane) {
+    const TR tr{};
     const int N = p.N, n = p.n;
     const double *kd = p.tab.kdiag + (size_t)g * N * 2;
     const double *lvlE = p.tab.lvlE + (size_t)g * N;
     const int32_t *mfirst = p.tab.mfirst + (size_t)g * N;
     const int32_t *msize = p.tab.msize + (size_t)g * N;
     const GridMeta meta = p.tab.meta[g];
-    const double *Mg = p.tab.M + (size_t)g * n * N * N;
+    const double *Rg = p.tab.R + (size_t)g * n * N * N;
     const double *Gg = p.tab.G + (size_t)g * n * N;
     const double t_half0 = half == 0 ? g * p.dt - p.tau : g * p.dt;
     double ell0 = ell, tau_rem = p.tau;
@@ -93,7 +103,7 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
             double s0 = 0.0, s1 = 0.0;
             for (int a = lane; a < N; a += 32) {
                 const double im = kd[2 * a + 1];
-                const double q = (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * exp(2.0 * im * t);
+                const double q = (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * lvl_exp(2.0 * im * t, tr);
                 s0 += q;
                 s1 += 2.0 * im * q;
             }
@@ -113,8 +123,8 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
             for (int a = lane; a < N; a += 32) {
                 const double re = kd[2 * a], im = kd[2 * a + 1];
                 double sn, cs;
-                sincos(re * t, &sn, &cs);
-                const double amp = exp(im * t);
+                lvl_sincos(re * t, &sn, &cs, tr);
+                const double amp = lvl_exp(im * t, tr);
                 const double2 v = c64[a];
                 const double2 r = make_double2(amp * (v.x * cs + v.y * sn), amp * (v.y * cs - v.x * sn));
                 c64[a] = r;
@@ -143,18 +153,19 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
             return -1.0;  // computed by the warp below
         };
         // manifold weight for non-singleton source manifolds (degenerate grids)
+        // (the rate depends on manifold energies only, so it sits inside R)
         auto manifold_w = [&](int al, int b) -> double {
             const int ms = msize[b];
-            const double *Ma = Mg + (size_t)al * N * N;
+            const double *Ra = Rg + (size_t)al * N * N;
             double acc = 0.0;
             for (int a = lane; a < N; a += 32) {
                 double yr = 0.0, yi = 0.0;
                 for (int bp = b; bp < b + ms; ++bp) {
-                    const double m = Ma[(size_t)a * N + bp];
+                    const double m = Ra[(size_t)a * N + bp];
                     yr += m * c64[bp].x;
                     yi += m * c64[bp].y;
                 }
-                acc += gamma_ohmic(lvlE[b] - lvlE[a], p.eta_g2, p.omega_c, p.beta) * (yr * yr + yi * yi);
+                acc += yr * yr + yi * yi;
             }
             return warp_sum(acc);
         };
@@ -223,20 +234,19 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
         }
         // stage two: target level a
         const int ms = msize[bsrc];
-        const double *Ma = Mg + (size_t)al_s * N * N;
+        const double *Ra = Rg + (size_t)al_s * N * N;
         auto target_w = [&](int a) -> double {
-            const double gm = gamma_ohmic(lvlE[bsrc] - lvlE[a], p.eta_g2, p.omega_c, p.beta);
             if (ms == 1) {
-                const double m = Ma[(size_t)a * N + bsrc];
-                return gm * m * m;
+                const double m = Ra[(size_t)a * N + bsrc];
+                return m * m;
             }
             double yr = 0.0, yi = 0.0;
             for (int bp = bsrc; bp < bsrc + ms; ++bp) {
-                const double m = Ma[(size_t)a * N + bp];
+                const double m = Ra[(size_t)a * N + bp];
                 yr += m * c64[bp].x;
                 yi += m * c64[bp].y;
             }
-            return gm * (yr * yr + yi * yi);
+            return yr * yr + yi * yi;
         };
         double tot2 = 0.0;
         for (int a = lane; a < N; a += 32) tot2 += target_w(a);
@@ -259,8 +269,7 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
             }
             double yr = 0.0, yi = 0.0;
             for (int bp = lo; bp < N && lvlE[bp] <= hi_e; ++bp) {
-                const double amp =
-                    sqrt(gamma_ohmic(lvlE[bp] - lvlE[a], p.eta_g2, p.omega_c, p.beta)) * Ma[(size_t)a * N + bp];
+                const double amp = Ra[(size_t)a * N + bp];
                 yr += amp * c64[bp].x;
                 yi += amp * c64[bp].y;
             }
@@ -294,7 +303,7 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
         // --- rest of the half-step: another crossing? ------------------------------
         double s0 = 0.0;
         for (int a = lane; a < N; a += 32)
-            s0 += (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * exp(2.0 * kd[2 * a + 1] * tau_rem);
+            s0 += (c64[a].x * c64[a].x + c64[a].y * c64[a].y) * lvl_exp(2.0 * kd[2 * a + 1] * tau_rem, tr);
         s0 = warp_sum(s0);
         if (tau_rem > 0.0 && log(s0) - logr <= 0.0) continue;
         break;
@@ -304,8 +313,8 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
     for (int a = lane; a < N; a += 32) {
         const double re = kd[2 * a], im = kd[2 * a + 1];
         double sn, cs;
-        sincos(re * tau_rem, &sn, &cs);
-        const double amp = exp(im * tau_rem);
+        lvl_sincos(re * tau_rem, &sn, &cs, tr);
+        const double amp = lvl_exp(im * tau_rem, tr);
         const double2 v = c64[a];
         const double2 r = make_double2(amp * (v.x * cs + v.y * sn), amp * (v.y * cs - v.x * sn));
         c64[a] = r;
@@ -323,6 +332,7 @@ static __device__ void resolve_half(const RunParams &p, int g, int half, int64_t
 
 // One frozen half-step in FP64 for a trajectory held in c64 (normalised):
 // propagate exactly when the threshold is not reached, resolve jumps when it is.
+template <typename TR>
 static __device__ void half_step64(const RunParams &p, int g, int half, int64_t traj, double2 *c64, double2 *y64,
                                    double &ell, double &logr, int &nj, int lane) {
     const int N = p.N;
@@ -342,7 +352,7 @@ static __device__ void half_step64(const RunParams &p, int g, int half, int64_t 
         __syncwarp();
         return;
     }
-    resolve_half(p, g, half, traj, c64, y64, ell, logr, nj, lane);
+    resolve_half<TR>(p, g, half, traj, c64, y64, ell, logr, nj, lane);
 }
 
 }  // namespace dev

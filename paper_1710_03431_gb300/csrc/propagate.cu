@@ -107,7 +107,7 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
     __syncwarp();
     double e = ell, lr = logr;
     int nj = sc.nj[t];
-    resolve_half(p, g, half, traj, c64, y64, e, lr, nj, lane);
+    resolve_half<R>(p, g, half, traj, c64, y64, e, lr, nj, lane);
     for (int a = lane; a < N; a += 32) {
         cre[a * LD + t] = (R)c64[a].x;
         cim[a * LD + t] = (R)c64[a].y;

@@ -49,6 +49,12 @@ constexpr int kStages = 4;
 constexpr int kSlots = 8;
 constexpr long long kWaitLimit = 1ll << 22;  // far above any legitimate wait (~100 us)
 
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -146,8 +152,8 @@ __device__ __forceinline__ void split_half(float x, __half &hi, __half &lo) {
 
 struct TcShared {
     // per-trajectory state (TT entries each), carved from dynamic smem
-    double *ell, *logr, *x;
-    float *kinv, *P, *fscale;  // 1/kappa of the stored operand, raw |D|^2, final-state scale
+    double *ell, *logr;
+    float *x, *kinv, *P, *fscale;  // observable, 1/kappa of the stored operand, raw |D|^2, final-state scale  // 1/kappa of the stored operand, raw |D|^2, final-state scale
     int *nj, *flag, *list;
     float *red;  // [4][NC/8][16]
     double *obs;
@@ -235,8 +241,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.obs = reinterpret_cast<double *>(misc + 112);                   // [2]
     S.ell = reinterpret_cast<double *>(misc + 128);
     S.logr = S.ell + TT;
-    S.x = S.logr + TT;
-    S.kinv = reinterpret_cast<float *>(S.x + TT);
+    S.x = reinterpret_cast<float *>(S.logr + TT);
+    S.kinv = S.x + TT;
     S.P = S.kinv + TT;
     S.fscale = S.P + TT;
     S.nj = reinterpret_cast<int *>(S.fscale + TT);
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const bool active = t0 + t < p.M;
             S.nj[t] = 0;
             S.kinv[t] = 1.0f;
-            S.x[t] = active ? 1.0 : 0.0;
+            S.x[t] = active ? 1.0f : 0.0f;
             if (active) {
                 S.logr[t] = log(uniform01(traj_event(p.seed, t0 + t, 0).x[0]));
                 const double l = log(p.tab.d2[0]);
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 double el = 0.0, lr = S.logr[t];
                 int nj = S.nj[t];
                 double2 *c64 = scr + (size_t)e * 2 * N;
-                half_step64(p, 0, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                half_step64<float>(p, 0, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
                 if (lane == 0) {
                     S.ell[t] = el;
                     S.logr[t] = lr;
@@ -422,13 +428,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
         // observable at s_0 (every active trajectory is in the ground state)
         if (e == 0) {
-            double sx = 0.0, sx2 = 0.0;
+            float sx = 0.f, sx2 = 0.f;
             for (int t = lane; t < TT; t += 32) {
                 sx += S.x[t];
                 sx2 += S.x[t] * S.x[t];
             }
-            sx = warp_sum(sx);
-            sx2 = warp_sum(sx2);
+            sx = warp_sumf(sx);
+            sx2 = warp_sumf(sx2);
             if (lane == 0) {
                 p.obs_part[((size_t)blockIdx.x * K) * 2] = sx;
                 p.obs_part[((size_t)blockIdx.x * K) * 2 + 1] = sx2;
@@ -564,7 +570,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     if (!cross) {
                         S.flag[t] = 0;
                         S.ell[t] = last ? lB : lA;
-                        S.x[t] = (double)(X / nB);
+                        S.x[t] = X / nB;
                         const float ko = S.kinv[t];
                         // kappa_g^2 = |O c|^2 (1 - dB)(1 - dA) with |O c|^2 = P kinv_{g-1}^2
                         S.kinv[t] = rsqrtf(Pt * ko * ko * (1.0f - dB) * (1.0f - dA));
@@ -617,16 +623,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     double el = S.ell[t], lr = S.logr[t];
                     int nj = S.nj[t];
                     double2 *c64 = scr + (size_t)e * 2 * N;
-                    half_step64(p, g, 0, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    half_step64<float>(p, g, 0, t0 + t, c64, c64 + N, el, lr, nj, lane);
                     double xs = 0.0;
                     for (int a = lane; a < gs; a += 32) xs += c64[a].x * c64[a].x + c64[a].y * c64[a].y;
                     xs = warp_sum(xs);
-                    if (!last) half_step64(p, g, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    if (!last) half_step64<float>(p, g, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
                     if (lane == 0) {
                         S.ell[t] = el;
                         S.logr[t] = lr;
                         S.nj[t] = nj;
-                        S.x[t] = xs;
+                        S.x[t] = (float)xs;
                         S.kinv[t] = 1.0f;
                     }
                 }
@@ -649,14 +655,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
             // ---- observable partials (fixed order) -----------------------------------------
             if (e == 0) {
-                double sx = 0.0, sx2 = 0.0;
+                // per-CTA partials of at most TT values in [0, 1]: FP32 is exact to
+                // ~1e-6 here; the partials are summed over CTAs in FP64
+                float sx = 0.f, sx2 = 0.f;
                 for (int t = lane; t < TT; t += 32) {
                     if (S.flag[t] == 2) continue;
                     sx += S.x[t];
                     sx2 += S.x[t] * S.x[t];
                 }
-                sx = warp_sum(sx);
-                sx2 = warp_sum(sx2);
+                sx = warp_sumf(sx);
+                sx2 = warp_sumf(sx2);
                 if (lane == 0) {
                     p.obs_part[((size_t)blockIdx.x * K + g) * 2] = sx;
                     p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = sx2;
@@ -678,7 +686,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
 size_t tc_smem_bytes(int N, int TT) {
     const int NC = 2 * TT;
     size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
-    b += 128 + (size_t)TT * (8 * 3 + 4 * 3 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
+    b += 128 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
     b = (b + 1023) & ~(size_t)1023;
     // one CTA per SM: the kernel allocates tensor-memory columns without sharing
     return b < 120 * 1024 ? 120 * 1024 : b;

@@ -101,7 +101,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.ehalf.assign((size_t)K * N * 2, 0.0);
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
-    tab.M.assign((size_t)K * n * NN, 0.0);
+    tab.R.assign((size_t)K * n * NN, 0.0);
     tab.lvlE.assign((size_t)K * N, 0.0);
     tab.mfirst.assign((size_t)K * N, 0);
     tab.msize.assign((size_t)K * N, 0);
@@ -216,7 +216,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         std::vector<double> VT(NN), W((size_t)N * (N / 2)), Wt((size_t)N * N);
         for (int x = 0; x < N; ++x)
             for (int a = 0; a < N; ++a) VT[(size_t)a * N + x] = V[(size_t)x * N + a];
-        double *Mg = &tab.M[(size_t)g * n * NN];
+        double *Mg = &tab.R[(size_t)g * n * NN];  // holds M_alpha until rescaled below
         for (int al = 0; al < n; ++al) {
             for (int a = 0; a < N; ++a) {
                 const double *va = &VT[(size_t)a * N];
@@ -283,6 +283,11 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                         }
                     }
             }
+        }
+        // jump operators with their rates absorbed (Eq. Aired): R = sqrt(gamma) M
+        for (int al = 0; al < n; ++al) {
+            double *Ma = Mg + (size_t)al * NN;
+            for (size_t ab = 0; ab < NN; ++ab) Ma[ab] *= std::sqrt(gam[ab]);
         }
         // half-step factors exp(-i K tau) and |.|^2
         double *eh = &tab.ehalf[(size_t)g * N * 2];

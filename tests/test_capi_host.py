@@ -96,8 +96,8 @@ def test_tables_match_oracle(aqt_lib, n, seed, s_idx):
         Ho = fr.eig.V @ np.diag(fr.eig.evals) @ fr.eig.V.T
         assert np.max(np.abs(H - Ho)) < 1e-12
         if fr.eig.nondegenerate:
-            Ml = A.aqt_debug_table(c, 3, g, (n, N, N))
-            assert np.max(np.abs(np.abs(Ml) - np.abs(fr.M))) < 1e-12
+            Rl = A.aqt_debug_table(c, 3, g, (n, N, N))
+            assert np.max(np.abs(np.abs(Rl) - np.abs(fr.R))) < 1e-12
             G = A.aqt_debug_table(c, 2, g, (n, N))
             Go = np.sum(fr.gam[None] * fr.M ** 2, axis=1)
             np.testing.assert_allclose(G, Go, rtol=1e-11, atol=1e-16)
