@@ -54,28 +54,30 @@ class Frame:
         # Bohr classes as level-pair masks (Eq. Lindblad2).
         self.classes = model.bohr_classes(eig)
         lm = eig.level_manifold
-        cid = np.full((len(eig.E), len(eig.E)), -1, dtype=int)
+        nm = len(eig.E)
+        cid = np.full((nm, nm), -1, dtype=int)
         for ci, (_, pairs) in enumerate(self.classes):
-            for ma, mb in pairs:
-                cid[ma, mb] = ci
+            if len(pairs) == 1:
+                cid[pairs[0]] = ci
+            else:
+                pa = np.array(pairs)
+                cid[pa[:, 0], pa[:, 1]] = ci
         self.class_of_pair = cid[lm[:, None], lm[None, :]]  # [a, b] -> class id
         # Sort the level pairs of each class into three evaluation shapes.
         order = np.argsort(self.class_of_pair, axis=None, kind="stable")
         flat = self.class_of_pair.reshape(-1)[order]
         starts = np.flatnonzero(np.r_[True, flat[1:] != flat[:-1]])
         ends = np.r_[starts[1:], len(flat)]
-        sing_a, sing_b, self.diag_classes, self.dense_classes = [], [], [], []
-        for st, en in zip(starts, ends):
+        sizes = ends - starts
+        single = starts[sizes == 1]
+        self.sing_a, self.sing_b = np.divmod(order[single], N)
+        self.diag_classes, self.dense_classes = [], []
+        for st, en in zip(starts[sizes > 1], ends[sizes > 1]):
             ia, ib = np.divmod(order[st:en], N)
-            if en - st == 1:
-                sing_a.append(ia[0])
-                sing_b.append(ib[0])
-            elif np.all(ia == ib):
+            if np.all(ia == ib):
                 self.diag_classes.append(ia)
             else:
                 self.dense_classes.append((ia, ib))
-        self.sing_a = np.array(sing_a, dtype=int)
-        self.sing_b = np.array(sing_b, dtype=int)
         # Rate of each singleton pair summed over alpha: sum_alpha R[alpha,a,b]^2.
         self.sing_rate = np.sum(self.R[:, self.sing_a, self.sing_b] ** 2, axis=0)
 

@@ -109,25 +109,26 @@ def bohr_classes(eig: Eigen):
     frequency omega = E(mb) - E(ma) (Sec. II, Eq. Lindblad2).
 
     Returns a list of (omega, [(ma, mb), ...]); the omega = 0 class, made of all
-    (m, m) pairs, comes first.
+    (m, m) pairs, comes first; the others follow in increasing omega.
     """
     nm = len(eig.E)
-    pairs = [(eig.E[mb] - eig.E[ma], ma, mb) for ma in range(nm) for mb in range(nm) if ma != mb]
-    pairs.sort()
+    ma, mb = np.meshgrid(np.arange(nm), np.arange(nm), indexing="ij")
+    off = ma != mb
+    ma, mb = ma[off], mb[off]
+    w = eig.E[mb] - eig.E[ma]
+    order = np.argsort(w, kind="stable")
+    w, ma, mb = w[order], ma[order], mb[order]
     classes = [(0.0, [(m, m) for m in range(nm)])]
-    cur = []
-    for w, ma, mb in pairs:
-        if cur and w - cur[-1][0] > eig.tol:
-            classes.append(_close_chain(cur, eig.tol))
-            cur = []
-        cur.append((w, ma, mb))
-    if cur:
-        classes.append(_close_chain(cur, eig.tol))
-    return classes
-
-
-def _close_chain(chain, tol):
-    ws = [w for w, _, _ in chain]
-    if ws[-1] - ws[0] > tol:
+    if len(w) == 0:
+        return classes
+    # chains: consecutive sorted frequencies no farther apart than tol
+    brk = np.flatnonzero(np.diff(w) > eig.tol) + 1
+    starts = np.r_[0, brk]
+    ends = np.r_[brk, len(w)]
+    if np.any(w[ends - 1] - w[starts] > eig.tol):
         raise ValueError("ambiguous Bohr-frequency grouping: chain wider than tolerance")
-    return (float(np.mean(ws)), [(ma, mb) for _, ma, mb in chain])
+    means = np.add.reduceat(w, starts) / (ends - starts)
+    mal, mbl = ma.tolist(), mb.tolist()
+    for ci, (st, en) in enumerate(zip(starts.tolist(), ends.tolist())):
+        classes.append((float(means[ci]), list(zip(mal[st:en], mbl[st:en]))))
+    return classes

@@ -3,7 +3,7 @@
 
 Calls only the oracle (split-exact AME, Sec. II Eqs. ME2-H / ME2-L on the
 symmetric split of the grid). Output: cfg_main_tf{10,100}_pgs.txt, one
-population per grid point. Run: python tests/golden/make_cfg_main_ame.py
+population per grid point. Run: python tests/golden/make_cfg_main_ame.py [t_f ...]
 """
 import os
 import sys
@@ -19,7 +19,8 @@ from oracle import ame  # noqa: E402
 
 
 def main():
-    for tf in (10.0, 100.0):
+    tfs = [float(a) for a in sys.argv[1:]] or [10.0, 100.0]
+    for tf in tfs:
         inst = W.cfg_main(t_f=tf)
         t = time.time()
         out = ame.run(inst)
