@@ -52,11 +52,16 @@ typedef enum {
     AQT_ENUMERIC = 5,   /* non-finite or non-positive norm, or too many jumps in one half-step */
     AQT_ENOCONV = 6,    /* eigensolver did not converge */
     AQT_EDEGEN = 7,     /* degenerate structure outside what the GPU path supports */
-    AQT_ENODEV = 8      /* context has no device (created with device -1) */
+    AQT_ENODEV = 8,     /* context has no device (created with device -1) */
+    AQT_ETIMEOUT = 9    /* a bounded wait inside the tensor-core kernel expired (about 2 s);
+                           the kernel stopped early and freed its resources; outputs are invalid */
 } aqt_status;
 
-/* Propagation precision of the rotation step (the jump clock, jump-time root,
- * channel draw and the tables are always FP64). */
+/* Propagation precision. The host tables and the jump clock are always FP64;
+ * the jump-time root, channel draw and jump operator run in the state's
+ * precision (FP64 for AQT_PREC_FP64, FP32 otherwise, with the norm decay kept
+ * as expm1 terms so that its relative accuracy does not depend on its size);
+ * the jump amplitude table is held in that precision on the device. */
 typedef enum {
     AQT_PREC_FP64 = 0,      /* SIMT FP64 state and rotation */
     AQT_PREC_FP32 = 1,      /* SIMT FP32 state and rotation, FP64 norm sums */
@@ -112,7 +117,10 @@ aqt_status aqt_set_grid(aqt_ctx *ctx, double t_f, int n_grid);
 aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int precision,
                                 int64_t jump_capacity);
 
-/* Device bytes the caller must provide for the current inputs. */
+/* Device bytes the caller must provide for the current inputs. Device runs
+ * take n_qubits <= 8 (N <= 256: the jump warp keeps N/32 levels per lane in
+ * registers) and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise AQT_EINVAL
+ * (host-only contexts build tables up to n_qubits = 10). */
 aqt_status aqt_workspace_size(aqt_ctx *ctx, size_t *bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, at least
@@ -134,7 +142,7 @@ aqt_status aqt_build_tables(aqt_ctx *ctx, void *stream);
 aqt_status aqt_run(aqt_ctx *ctx, void *stream);
 
 /* Wait for the last run and return its device status: AQT_OK, AQT_EOVERFLOW
- * (jump records dropped) or AQT_ENUMERIC. */
+ * (jump records dropped), AQT_ENUMERIC or AQT_ETIMEOUT. */
 aqt_status aqt_sync(aqt_ctx *ctx);
 
 /* Ground-manifold population at each grid point: mean[n_grid] and the
@@ -162,8 +170,9 @@ aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
  * (aqt_build_tables must have run on a bound workspace) and writes to the
  * caller's device outputs: obs_sums[n_grid][2] (sum of x, sum of x^2),
  * final_states[M][N][2] (eigenbasis, FP64), jumps[jump_capacity] (unsorted),
- * *jump_count (records produced, kept or not) and *status (0, or 2 for a
- * numeric problem). The kernel's scratch -- per-CTA observable partials and
+ * *jump_count (records produced, kept or not) and *status (0; bit 1 for a
+ * numeric problem; bit 2 when a bounded wait of the tensor-core kernel
+ * expired, with bits 8-13 naming the wait). The kernel's scratch -- per-CTA observable partials and
  * FP64 jump vectors -- comes from one 32 MiB array compiled into the library,
  * held on every GPU that loads the library until the process exits. No
  * device memory is allocated by this call.
@@ -183,8 +192,12 @@ aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, 
 
 /* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes
- * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N]; 4 frame rotation O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1);
- * 5 eigenvectors V [N][N] (column a = level a); 6 manifold energy per level [N]. */
+ * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N] (held in
+ * FP32 unless the precision is AQT_PREC_FP64); 4 frame rotation
+ * O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1); 5 eigenvectors V [N][N]
+ * (column a = level a); 6 manifold energy per level [N]; 7 grid metadata [4]:
+ * (some manifold degenerate, ground-manifold size, every Bohr class of
+ * nonzero frequency is a single manifold pair, energy tolerance). */
 aqt_status aqt_debug_table(aqt_ctx *ctx, int which, int grid, double *out);
 
 #ifdef __cplusplus

@@ -14,10 +14,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaqt.so")
 
-AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV = range(9)
+AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV, AQT_ETIMEOUT = range(10)
 AQT_PREC_FP64, AQT_PREC_FP32, AQT_PREC_F16SPLIT = 0, 1, 2
 STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4: "AQT_EOVERFLOW",
-                5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV"}
+                5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV", 9: "AQT_ETIMEOUT"}
 
 EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
            "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",

@@ -34,6 +34,8 @@ bool sym_eigen(int n, double *A, double *evals, double *V);
 struct GridMeta {
     int32_t degenerate;  // some degenerate manifold has more than one level
     int32_t gs_size;     // size of the lowest manifold (observable support)
+    int32_t simple;      // every Bohr class of nonzero frequency holds one manifold pair
+    int32_t pad;
     double tol;          // energy tolerance for manifolds and Bohr classes
 };
 
@@ -46,7 +48,10 @@ struct Tables {
     std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
     std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
     std::vector<double> G;       // [K][n][N]  sum_a gamma(w_ab) M_alpha[a,b]^2
-    std::vector<double> R;       // [K][n][N][N] R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b], M_alpha = V^T sz_alpha V
+    // jump amplitudes, source-major: Rt[g][alpha][b][a] = R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b],
+    // M_alpha = V^T sz_alpha V; FP64 for the FP64 path, FP32 (Rt32) for the others
+    std::vector<double> Rt;      // [K][n][N][N]
+    std::vector<float> Rt32;     // [K][n][N][N]
     std::vector<double> lvlE;    // [K][N]     energy of each level's manifold
     std::vector<int32_t> mfirst; // [K][N]     first level of each level's manifold
     std::vector<int32_t> msize;  // [K][N]     size of each level's manifold
@@ -73,7 +78,8 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
 
 // ------------------------------------------------------------- kernels ------
 struct DevTables {
-    const double *kdiag, *ehalf, *d2, *G, *R, *lvlE;
+    const double *kdiag, *ehalf, *d2, *G, *lvlE;
+    const void *Rt;     // [g][alpha][b][a]: double (FP64 path) or float
     const float *ehalf32;
     const int32_t *mfirst, *msize;
     const GridMeta *meta;
@@ -94,9 +100,15 @@ struct RunParams {
     unsigned long long *jcount;
     double *obs_part;              // [n_cta][K][2]
     double *obs_sum;               // [K][2]
-    double *scratch;               // [n_cta][8][2][N][2] FP64 jump scratch
+    double *scratch;               // [n_cta][kScratchSlots][kSlotDouble2 * N][2] jump scratch
     int32_t *status;
 };
+
+// Jump scratch per warp (SIMT) or jump slot (tensor-core path), in double2
+// units per level: two FP64 vectors for the general jump operator, then one
+// FP32 state (real, imaginary planes) handed between the epilogue warps.
+constexpr int kSlotDouble2 = 3;
+constexpr int kScratchSlots = 8;
 
 // Launch the propagation (precision per aqt_precision) and the observable
 // reduction on `stream`. Returns a CUDA error code (0 on success).

@@ -86,7 +86,7 @@ void compute_layout(aqt_ctx *c) {
     L.ehalf32 = take(K * N * 2 * 4);
     L.d2 = take(K * N * 8);
     L.G = take(K * n * N * 8);
-    L.R = take(K * n * N * N * 8);
+    L.R = take(K * n * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
     L.lvlE = take(K * N * 8);
     L.mfirst = take(K * N * 4);
     L.msize = take(K * N * 4);
@@ -98,9 +98,18 @@ void compute_layout(aqt_ctx *c) {
     L.jcount = take(8);
     L.obs_part = take((size_t)c->n_cta * K * 2 * 8);
     L.obs_sum = take(K * 2 * 8);
-    L.scratch = take((size_t)c->n_cta * 8 * 2 * N * 2 * 8);
+    L.scratch = take((size_t)c->n_cta * kScratchSlots * kSlotDouble2 * N * 16);
     L.status = take(4);
     L.total = off;
+}
+
+// Sizes the device paths take: the jump warp holds N/32 levels per lane in
+// registers (at most 8, so N <= 256); the tensor-core tiles take N = 128 or 256.
+aqt_status device_shape_check(aqt_ctx *c) {
+    if (c->in.n > 8) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 8 (N <= 256)");
+    if (c->in.precision == AQT_PREC_F16SPLIT && c->in.n < 7)
+        return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
+    return AQT_OK;
 }
 
 aqt_status use_device(aqt_ctx *c) {
@@ -123,12 +132,13 @@ size_t run_smem(const aqt_ctx *c) { return c->smem; }
 
 aqt_status static_scratch_need(aqt_ctx *c, size_t *bytes) {
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs first");
-    aqt_status s = use_device(c);
+    aqt_status s = device_shape_check(c);
+    if (s == AQT_OK) s = use_device(c);
     if (s != AQT_OK) return s;
     compute_layout(c);
     const size_t N = (size_t)1 << c->in.n, K = c->in.K;
     const size_t part = ((size_t)c->n_cta * K * 2 * 8 + 255) & ~(size_t)255;
-    *bytes = part + (size_t)c->n_cta * 8 * 2 * N * 2 * 8;
+    *bytes = part + (size_t)c->n_cta * kScratchSlots * kSlotDouble2 * N * 16;
     return AQT_OK;
 }
 
@@ -157,7 +167,7 @@ aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
     p->tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
     p->tab.d2 = (const double *)(c->ws + L.d2);
     p->tab.G = (const double *)(c->ws + L.G);
-    p->tab.R = (const double *)(c->ws + L.R);
+    p->tab.Rt = c->ws + L.R;
     p->tab.lvlE = (const double *)(c->ws + L.lvlE);
     p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p->tab.msize = (const int32_t *)(c->ws + L.msize);
@@ -278,8 +288,8 @@ aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precis
 aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set ising, schedule, bath, grid and trajectories first");
-    if (c->in.precision == AQT_PREC_F16SPLIT && (c->in.n < 7 || c->in.n > 8))
-        return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
+    aqt_status s = device_shape_check(c);
+    if (s != AQT_OK) return s;
     compute_layout(c);
     *bytes = c->lay.total;
     return AQT_OK;
@@ -288,6 +298,8 @@ aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
 aqt_status aqt_bind_workspace(aqt_ctx *c, void *dptr, size_t bytes) {
     if (!c) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs before binding a workspace");
+    aqt_status s = device_shape_check(c);
+    if (s != AQT_OK) return s;
     compute_layout(c);
     if (!dptr || ((uintptr_t)dptr & 255)) return fail(c, AQT_EINVAL, "workspace must be 256-byte aligned");
     if (bytes < c->lay.total) return fail(c, AQT_ENOMEM, "workspace smaller than aqt_workspace_size");
@@ -327,7 +339,8 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     if (!e) e = put(L.ehalf32, e32.data(), e32.size() * 4);
     if (!e) e = put(L.d2, t.d2.data(), t.d2.size() * 8);
     if (!e) e = put(L.G, t.G.data(), t.G.size() * 8);
-    if (!e) e = put(L.R, t.R.data(), t.R.size() * 8);
+    if (!e && !t.Rt.empty()) e = put(L.R, t.Rt.data(), t.Rt.size() * 8);
+    if (!e && !t.Rt32.empty()) e = put(L.R, t.Rt32.data(), t.Rt32.size() * 4);
     if (!e) e = put(L.lvlE, t.lvlE.data(), t.lvlE.size() * 8);
     if (!e) e = put(L.mfirst, t.mfirst.data(), t.mfirst.size() * 4);
     if (!e) e = put(L.msize, t.msize.data(), t.msize.size() * 4);
@@ -407,7 +420,7 @@ aqt_status aqt_run(aqt_ctx *c, void *stream) {
     p.tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
     p.tab.d2 = (const double *)(c->ws + L.d2);
     p.tab.G = (const double *)(c->ws + L.G);
-    p.tab.R = (const double *)(c->ws + L.R);
+    p.tab.Rt = c->ws + L.R;
     p.tab.lvlE = (const double *)(c->ws + L.lvlE);
     p.tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p.tab.msize = (const int32_t *)(c->ws + L.msize);
@@ -441,6 +454,14 @@ aqt_status aqt_sync(aqt_ctx *c) {
     e = cudaMemcpy(&status, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost);
     if (!e) e = cudaMemcpy(&cnt, c->ws + c->lay.jcount, 8, cudaMemcpyDeviceToHost);
     if (e) return cuda_fail(c, e, "status readback");
+    if (status & 4) {
+        std::string where;
+        static const char *site[] = {"producer ring slot", "producer drain", "B operand ready", "ring stage full",
+                                     "product done", "abort drain"};
+        for (int i = 0; i < 6; ++i)
+            if (status & (1 << (8 + i))) where += std::string(where.empty() ? "" : ", ") + site[i];
+        return fail(c, AQT_ETIMEOUT, "a bounded wait expired in the tensor-core kernel (" + where + ")");
+    }
     if (status & 2) return fail(c, AQT_ENUMERIC, "non-finite norm or too many jumps in one half-step");
     if ((int64_t)cnt > c->in.jcap)
         return fail(c, AQT_EOVERFLOW, "jump log full: " + std::to_string((int64_t)cnt - c->in.jcap) + " dropped");
@@ -543,13 +564,26 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
         case 0: std::copy_n(&t.evals[g * N], N, out); break;
         case 1: std::copy_n(&t.kdiag[g * N * 2], N * 2, out); break;
         case 2: std::copy_n(&t.G[g * n * N], n * N, out); break;
-        case 3: std::copy_n(&t.R[g * n * NN], n * NN, out); break;
+        case 3:
+            for (size_t al = 0; al < n; ++al)
+                for (size_t a = 0; a < N; ++a)
+                    for (size_t b = 0; b < N; ++b) {
+                        const size_t i = (g * n + al) * NN + b * N + a;
+                        out[al * NN + a * N + b] = t.Rt.empty() ? (double)t.Rt32[i] : t.Rt[i];
+                    }
+            break;
         case 4:
             for (size_t a = 0; a < N; ++a)
                 for (size_t b = 0; b < N; ++b) out[a * N + b] = t.OT[g * NN + b * N + a];
             break;
         case 5: std::copy_n(&t.V[g * NN], NN, out); break;
         case 6: std::copy_n(&t.lvlE[g * N], N, out); break;
+        case 7:
+            out[0] = t.meta[g].degenerate;
+            out[1] = t.meta[g].gs_size;
+            out[2] = t.meta[g].simple;
+            out[3] = t.meta[g].tol;
+            break;
         default: return fail(c, AQT_EINVAL, "unknown table");
     }
     return AQT_OK;

@@ -10,9 +10,9 @@
 //   half-step frozen at s_g (first half of the next interval)
 // with K the diagonal eigenframe H_eff (Sec. III, Eq. Heff). When ell falls to
 // log r inside a half-step (Sec. IV; App. C), the warp that owns the
-// trajectory finds the crossing time in FP64, draws the jump (App. B.1,
-// Eq. Pi(t)), applies it (Eq. jump), draws a new threshold and finishes the
-// half-step, possibly jumping again.
+// trajectory finds the crossing time, draws the jump (App. B.1, Eq. Pi(t)),
+// applies it (Eq. jump), draws a new threshold and finishes the half-step,
+// possibly jumping again (device_jump.cuh).
 //
 // Layout: one CTA owns TT trajectories for the whole run; their states stay in
 // shared memory as planar real/imaginary [level][trajectory] tiles. The frame
@@ -70,7 +70,7 @@ __device__ __forceinline__ const double *ehalf_table<double>(const RunParams &p)
 // One trajectory's renormalisation, frozen half-step and crossing check.
 template <typename R>
 __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t traj, R *cre, R *cim, int LD,
-                          const R *eh, const double *d2s, Scalars sc, double2 *c64, double2 *y64, int lane) {
+                          const R *eh, const double *d2s, Scalars sc, double2 *c64, int lane) {
     const int N = p.N;
     double nu = 0.0, f = 0.0;
     for (int a = lane; a < N; a += 32) {
@@ -100,28 +100,12 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
         __syncwarp();
         return;
     }
-    // crossing inside this half-step: FP64 jump resolution
-    const double inv = 1.0 / sqrt(nu);
-    for (int a = lane; a < N; a += 32)
-        c64[a] = make_double2((double)cre[a * LD + t] * inv, (double)cim[a * LD + t] * inv);
-    __syncwarp();
-    double e = ell, lr = logr;
-    int nj = sc.nj[t];
-    resolve_half<R>(p, g, half, traj, c64, y64, e, lr, nj, lane);
-    for (int a = lane; a < N; a += 32) {
-        cre[a * LD + t] = (R)c64[a].x;
-        cim[a * LD + t] = (R)c64[a].y;
-    }
-    if (lane == 0) {
-        sc.ell[t] = e;
-        sc.logr[t] = lr;
-        sc.nj[t] = nj;
-    }
-    __syncwarp();
+    // crossing inside this half-step: the warp resolves it with the state in registers
+    jump_half_step_any<R>(p, g, half, traj, cre + t, cim + t, LD, &sc.ell[t], &sc.logr[t], &sc.nj[t], lane, c64);
 }
 
 template <typename R, int RA>
-__global__ void __launch_bounds__(kThreads) propagate_simt(RunParams p) {
+__global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.N, K = p.K, TT = p.TT;
     const int LD = TT + 4;
@@ -141,8 +125,8 @@ __global__ void __launch_bounds__(kThreads) propagate_simt(RunParams p) {
     Scalars sc{logr, ell, nj};
 
     const int64_t t0 = (int64_t)blockIdx.x * TT;
-    double2 *c64 = reinterpret_cast<double2 *>(p.scratch) + ((size_t)blockIdx.x * kWarps + warp) * 2 * N;
-    double2 *y64 = c64 + N;
+    static_assert(kWarps <= kScratchSlots, "one jump scratch slot per warp");
+    double2 *c64 = reinterpret_cast<double2 *>(p.scratch) + ((size_t)blockIdx.x * kScratchSlots + warp) * kSlotDouble2 * N;
 
     // initial state: ground state of H_S(0) (level 0), threshold from event 0
     for (int i = tid; i < N * LD; i += kThreads) {
@@ -195,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) propagate_simt(RunParams p) {
     auto half_all = [&](int g, int half) {
         for (int t = warp; t < TT; t += kWarps) {
             if (t0 + t >= p.M) continue;
-            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, y64, lane);
+            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, lane);
         }
     };
 

@@ -15,9 +15,9 @@
 //           half-steps around s_g with the exact diagonal factors, test the
 //           norm-threshold jump clock in FP64, accumulate the observable, and
 //           write the next step's C_hi/C_lo operand back into shared memory.
-// Trajectories whose clock crosses its threshold are handed, in FP64, to the
-// same jump resolution as the SIMT kernel (App. C; App. B.1, Eq. Pi(t);
-// Eq. jump), one epilogue warp per trajectory.
+// Trajectories whose clock crosses its threshold are handed to the same jump
+// resolution as the SIMT kernel (App. C; App. B.1, Eq. Pi(t); Eq. jump), one
+// epilogue warp per trajectory, state in registers.
 //
 // Operand layouts (no swizzle, 8x16-byte core matrices):
 //   A = O block [N rows][16 cols], K-major: core (r/8, k/8) at ((r/8)*2 + k/8)*128 B
@@ -46,8 +46,11 @@ constexpr int kEpiWarps = 12;                       // 3 column groups x 4 TMEM 
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kTcThreads = 64 + kEpiThreads;
 constexpr int kStages = 4;
-constexpr int kSlots = 8;
-constexpr long long kWaitLimit = 1ll << 22;  // far above any legitimate wait (~100 us)
+constexpr int kSlots = kScratchSlots;
+constexpr long long kWaitLimit = 1ll << 22;           // polls, and
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait (~1 ms)
+// wait sites, reported as status bits 8.. next to kStatusTimeout
+enum : int { kSiteSlot = 0, kSiteDrain, kSiteBReady, kSiteFull, kSiteDFull, kSiteAbort };
 
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -76,14 +79,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false (and the abort flag set) when the limit expires.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *status) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait (poll count and wall time, since one try_wait may suspend the
+// thread for a while): false, with the abort flag set and the site recorded,
+// when the limit expires.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *status, int site) {
+    const unsigned long long t0 = global_ns();
     for (long long i = 0; i < kWaitLimit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
+        if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) break;
     }
     *abort_flag = 1;
-    atomicOr(status, kStatusTimeout);
+    atomicOr(status, kStatusTimeout | (1 << (8 + site)));
     return false;
 }
 
@@ -285,7 +298,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 for (int kb = 0; kb < NK; ++kb, ++it) {
                     const int slot = (int)(it % kStages);
                     if (it >= kStages &&
-                        !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1), S.abort_flag, p.status))
+                        !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1), S.abort_flag, p.status,
+                                   kSiteSlot))
                         break;
                     mbar_expect_tx(bar_full + 8 * slot, stage_bytes);
                     bulk_g2s(smem_u32(sA + (size_t)slot * stage_bytes),
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             // drain: wait (bounded) for the copies still in flight
             for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
                 if (!mbar_wait(bar_full + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), S.abort_flag,
-                               p.status))
+                               p.status, kSiteDrain))
                     break;
         }
     } else if (warp == 1) {
@@ -309,12 +323,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             long long it = 0;
             uint32_t last_bar = 0, last_par = 0;
             for (int g = 1; g < K; ++g) {
-                if (!mbar_wait(bar_bready, (uint32_t)((g - 1) & 1), S.abort_flag, p.status)) break;
+                if (!mbar_wait(bar_bready, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteBReady)) break;
                 fence_after();
                 bool ok = true;
                 for (int kb = 0; kb < NK; ++kb, ++it) {
                     const int slot = (int)(it % kStages);
-                    if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status)) {
+                    if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status,
+                                   kSiteFull)) {
                         ok = false;
                         break;
                     }
@@ -340,8 +355,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             // on an abort, let the products already issued finish (bounded)
             // before the tensor memory is released
             if (*S.abort_flag && last_bar) {
-                for (long long i = 0; i < kWaitLimit; ++i)
+                const unsigned long long ta = global_ns();
+                for (long long i = 0; i < kWaitLimit; ++i) {
                     if (mbar_try(last_bar, last_par)) break;
+                    if ((i & 255) == 255 && global_ns() - ta > kWaitNs) {
+                        atomicOr(p.status, kStatusTimeout | (1 << (8 + kSiteAbort)));
+                        break;
+                    }
+                }
             }
         }
     } else {
@@ -349,7 +370,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;  // ch: column group 0..2
         const int nchunk = NC / 8;
         const int c_begin = (ch * nchunk) / 3, c_end = ((ch + 1) * nchunk) / 3;
-        double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * 2 * N;
+        // jump slots: general-jump scratch (2N double2), then the FP32 state planes
+        double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * kSlotDouble2 * N;
+        auto slot_re = [&](int sidx) { return reinterpret_cast<float *>(scr + ((size_t)sidx * kSlotDouble2 + 2) * N); };
         const float4 *lvl = reinterpret_cast<const float4 *>(p.tab.tclvl);
 
         // ---- initial state e_0 and the half-step after s_0 ------------------------
@@ -392,21 +415,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
         }
         epi_sync();
-        // crossed at the first half-step: FP64 resolution from e_0
+        // crossed at the first half-step: warp resolution from e_0
         for (int base = 0; base < *S.count; base += kSlots) {
             const int nr = min(kSlots, *S.count - base);
             for (int sidx = 0; sidx < nr; ++sidx)
                 for (int h = 0; h < MH; ++h) {
                     const int a = 128 * h + 32 * q + lane;
-                    if (ch == 0) scr[(size_t)sidx * 2 * N + a] = make_double2(a == 0 ? 1.0 : 0.0, 0.0);
+                    if (ch == 0) {
+                        slot_re(sidx)[a] = a == 0 ? 1.0f : 0.0f;
+                        slot_re(sidx)[N + a] = 0.0f;
+                    }
                 }
             epi_sync();
             if (e < nr) {
                 const int t = S.list[base + e];
                 double el = 0.0, lr = S.logr[t];
                 int nj = S.nj[t];
-                double2 *c64 = scr + (size_t)e * 2 * N;
-                half_step64<float>(p, 0, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                float *sre = slot_re(e);
+                jump_half_step<float, 4 * MH>(p, 0, 1, t0 + t, sre, sre + N, 1, el, lr, nj, lane,
+                                              scr + (size_t)e * kSlotDouble2 * N);
                 if (lane == 0) {
                     S.ell[t] = el;
                     S.logr[t] = lr;
@@ -419,8 +446,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 for (int h = 0; h < MH; ++h) {
                     const int a = 128 * h + 32 * q + lane;
                     if (ch == 0) {
-                        const double2 v = scr[(size_t)sidx * 2 * N + a];
-                        store_one(sB_hi, sB_lo, NC, a, t, v.x, v.y);
+                        const float *sre = slot_re(sidx);
+                        store_one(sB_hi, sB_lo, NC, a, t, sre[a], sre[N + a]);
                     }
                 }
             }
@@ -456,7 +483,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const bool last = g == K - 1;
             // one thread waits for the products; all epilogue threads then take
             // the same decision (a bounded wait can expire for one thread only)
-            if (etid == 0) *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status) ? 1 : 0;
+            if (etid == 0)
+                *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
             epi_sync();
             if (!*S.epi_ok) break;
             fence_after();
@@ -600,7 +628,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         }
                     }
             }
-            // ---- crossed trajectories: FP64 resolution of both half-steps ---------------------
+            // ---- crossed trajectories: warp resolution of both half-steps ---------------------
             const int ncross = *S.count;
             for (int base = 0; base < ncross; base += kSlots) {
                 const int nr = min(kSlots, ncross - base);
@@ -613,7 +641,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                             const int a = 128 * h + 32 * q + lane;
                             float d[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
-                            scr[(size_t)sidx * 2 * N + a] = make_double2(d[2 * j] * inv, d[2 * j + 1] * inv);
+                            slot_re(sidx)[a] = d[2 * j] * inv;
+                            slot_re(sidx)[N + a] = d[2 * j + 1] * inv;
                         }
                     }
                 }
@@ -622,12 +651,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     const int t = S.list[base + e];
                     double el = S.ell[t], lr = S.logr[t];
                     int nj = S.nj[t];
-                    double2 *c64 = scr + (size_t)e * 2 * N;
-                    half_step64<float>(p, g, 0, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    float *sre = slot_re(e);
+                    double2 *slow = scr + (size_t)e * kSlotDouble2 * N;
+                    jump_half_step<float, 4 * MH>(p, g, 0, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow);
                     double xs = 0.0;
-                    for (int a = lane; a < gs; a += 32) xs += c64[a].x * c64[a].x + c64[a].y * c64[a].y;
+                    for (int a = lane; a < gs; a += 32) xs += (double)sre[a] * sre[a] + (double)sre[N + a] * sre[N + a];
                     xs = warp_sum(xs);
-                    if (!last) half_step64<float>(p, g, 1, t0 + t, c64, c64 + N, el, lr, nj, lane);
+                    if (!last)
+                        jump_half_step<float, 4 * MH>(p, g, 1, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow);
                     if (lane == 0) {
                         S.ell[t] = el;
                         S.logr[t] = lr;
@@ -641,13 +672,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     const int t = S.list[base + sidx];
                     for (int h = 0; h < MH; ++h) {
                         const int a = 128 * h + 32 * q + lane;
-                        const double2 v = scr[(size_t)sidx * 2 * N + a];
+                        const float vr = slot_re(sidx)[a], vi = slot_re(sidx)[N + a];
                         if (!last) {
-                            store_one(sB_hi, sB_lo, NC, a, t, v.x, v.y);
+                            store_one(sB_hi, sB_lo, NC, a, t, vr, vi);
                         } else {
                             double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
-                            fs[0] = v.x;
-                            fs[1] = v.y;
+                            fs[0] = vr;
+                            fs[1] = vi;
                         }
                     }
                 }

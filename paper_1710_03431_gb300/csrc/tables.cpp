@@ -101,11 +101,13 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.ehalf.assign((size_t)K * N * 2, 0.0);
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
-    tab.R.assign((size_t)K * n * NN, 0.0);
+    const bool r64 = in.precision == AQT_PREC_FP64;
+    tab.Rt.assign(r64 ? (size_t)K * n * NN : 0, 0.0);
+    tab.Rt32.assign(r64 ? 0 : (size_t)K * n * NN, 0.0f);
     tab.lvlE.assign((size_t)K * N, 0.0);
     tab.mfirst.assign((size_t)K * N, 0);
     tab.msize.assign((size_t)K * N, 0);
-    tab.meta.assign(K, GridMeta{0, 1, 0.0});
+    tab.meta.assign(K, GridMeta{0, 1, 1, 0, 0.0});
     tab.OT.assign((size_t)(K - 1) * NN, 0.0);
 
     // classical energies sum_i hz_i z_i + sum_{i<j} J_ij z_i z_j, z = 1 - 2 bit
@@ -190,7 +192,9 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
             fail(AQT_EDEGEN, "ground state of H_S(0) is degenerate: the initial state is ambiguous");
             return;
         }
-        // Bohr classes over manifold pairs must be tight chains.
+        // Bohr classes over manifold pairs must be tight chains; a grid point is
+        // "simple" when every class of nonzero frequency holds one manifold pair.
+        meta.simple = 1;
         {
             const size_t nm = E.size();
             std::vector<double> w;
@@ -202,6 +206,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
             size_t st0 = 0;
             for (size_t i = 1; i <= w.size(); ++i) {
                 if (i == w.size() || w[i] - w[i - 1] > tol) {
+                    if (i - st0 > 1) meta.simple = 0;
                     if (i > 0 && w[i - 1] - w[st0] > tol) {
                         fail(AQT_EDEGEN, "ambiguous Bohr-frequency grouping at grid point " + std::to_string(g));
                         return;
@@ -216,7 +221,8 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         std::vector<double> VT(NN), W((size_t)N * (N / 2)), Wt((size_t)N * N);
         for (int x = 0; x < N; ++x)
             for (int a = 0; a < N; ++a) VT[(size_t)a * N + x] = V[(size_t)x * N + a];
-        double *Mg = &tab.R[(size_t)g * n * NN];  // holds M_alpha until rescaled below
+        std::vector<double> Mbuf((size_t)n * NN);
+        double *Mg = Mbuf.data();
         for (int al = 0; al < n; ++al) {
             for (int a = 0; a < N; ++a) {
                 const double *va = &VT[(size_t)a * N];
@@ -284,10 +290,18 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                     }
             }
         }
-        // jump operators with their rates absorbed (Eq. Aired): R = sqrt(gamma) M
+        // jump operators with their rates absorbed (Eq. Aired): R = sqrt(gamma) M,
+        // stored source-major (Rt[b][a] = R[a][b]; M is symmetric)
+        for (auto &x : gam) x = std::sqrt(x);
         for (int al = 0; al < n; ++al) {
-            double *Ma = Mg + (size_t)al * NN;
-            for (size_t ab = 0; ab < NN; ++ab) Ma[ab] *= std::sqrt(gam[ab]);
+            const double *Ma = Mg + (size_t)al * NN;
+            const size_t base = ((size_t)g * n + al) * NN;
+            for (int b = 0; b < N; ++b)
+                for (int a = 0; a < N; ++a) {
+                    const double r = gam[(size_t)a * N + b] * Ma[(size_t)b * N + a];
+                    if (r64) tab.Rt[base + (size_t)b * N + a] = r;
+                    else tab.Rt32[base + (size_t)b * N + a] = (float)r;
+                }
         }
         // half-step factors exp(-i K tau) and |.|^2
         double *eh = &tab.ehalf[(size_t)g * N * 2];

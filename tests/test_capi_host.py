@@ -116,3 +116,51 @@ def test_degenerate_ground_state_rejected(aqt_lib):
     with pytest.raises(A.AqtError) as e:
         A.aqt_build_tables(c, 0)
     assert e.value.status == A.AQT_EDEGEN
+
+
+@pytest.mark.parametrize("n,seed,grid,idx", [(3, 7, 11, [0, 1, 5, 10]), (4, 1710_03431, 201, [0, 1, 2, 50, 200])])
+def test_grid_metadata_matches_oracle(aqt_lib, n, seed, grid, idx):
+    """Manifold and Bohr-class bookkeeping that selects the jump operator's
+    form: degenerate manifolds, ground-manifold size, and whether every class
+    of nonzero frequency is one manifold pair (Eq. Lindblad2)."""
+    from oracle import model
+    A = aqt_lib
+    inst = W.tfim_instance(n, seed, n_grid=grid)
+    c = _host_ctx(A, inst)
+    A.aqt_build_tables(c, 0)
+    terms = model.hamiltonian_terms(inst)
+    for g in idx:
+        eig = model.eigen_at(inst, g / (grid - 1), terms)
+        meta = A.aqt_debug_table(c, 7, g, (4,))
+        classes = model.bohr_classes(eig)
+        simple = all(len(pairs) == 1 for _, pairs in classes[1:])
+        assert bool(meta[0]) == (not eig.nondegenerate), g
+        assert int(meta[1]) == int(np.sum(eig.level_manifold == 0)), g
+        assert bool(meta[2]) == simple, g
+        assert meta[3] == pytest.approx(eig.tol, rel=1e-15), g
+    A.aqt_destroy(c)
+
+
+def test_fp32_jump_table_is_rounded_fp64(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(3, 7, n_grid=5)
+    c64 = _host_ctx(A, inst, precision=0)
+    c32 = _host_ctx(A, inst, precision=1)
+    A.aqt_build_tables(c64, 0)
+    A.aqt_build_tables(c32, 0)
+    for g in (1, 4):
+        r64 = A.aqt_debug_table(c64, 3, g, (3, 8, 8))
+        r32 = A.aqt_debug_table(c32, 3, g, (3, 8, 8))
+        np.testing.assert_array_equal(r32, r64.astype(np.float32).astype(np.float64))
+    A.aqt_destroy(c64)
+    A.aqt_destroy(c32)
+
+
+def test_device_runs_limited_to_256_levels(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(9, 3, n_grid=3)
+    c = _host_ctx(A, inst)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_workspace_size(c)
+    assert e.value.status == A.AQT_EINVAL
+    A.aqt_destroy(c)
