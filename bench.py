@@ -276,7 +276,8 @@ def run_ours(args):
         rs = 8 if prec == A.AQT_PREC_FP64 else 4
         tcl = K * N * 16 if prec == A.AQT_PREC_F16SPLIT else 0
         n = inst.n_qubits
-        h2d = (K * N * (2 * 8 + 2 * 8 + 2 * 4 + 8 + 8 + 4 + 4) + K * n * N * 8 + K * n * N * N * 8 + K * 16
+        # the tables aqt_build_tables copies (jump amplitudes and rotations in the state precision)
+        h2d = (K * N * (2 * 8 + 2 * 8 + 2 * 4 + 8 + 8 + 4 + 4) + K * n * N * 8 + K * n * N * N * rs + K * 24
                + (K - 1) * N * N * rs + tcl)
         e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(K * 2 * 8 + 12), "seconds_per_step": e2e_s,
