@@ -114,6 +114,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// Fetch [src, src + bytes) into L2 (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -293,8 +298,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         // ---------------- bulk-copy producer ----------------
         if (lane == 0) {
             const unsigned char *src = reinterpret_cast<const unsigned char *>(p.tab.OT);
+            // every CTA reads the same rotation tile in each step; each warms L2 with
+            // its slice of the tile one step ahead, so the ring's copies hit L2
+            const size_t tile = (size_t)NK * stage_bytes;
+            const size_t piece = ((tile + p.n_cta - 1) / p.n_cta + 15) & ~(size_t)15;
+            const size_t poff = (size_t)blockIdx.x * piece;
+            auto warm = [&](int tg) {
+                if (tg < K - 1 && poff < tile)
+                    l2_prefetch(src + (size_t)tg * tile + poff, (uint32_t)(piece < tile - poff ? piece : tile - poff));
+            };
+            warm(0);
             long long it = 0;
             for (int g = 1; g < K && !*S.abort_flag; ++g) {
+                warm(g);
                 for (int kb = 0; kb < NK; ++kb, ++it) {
                     const int slot = (int)(it % kStages);
                     if (it >= kStages &&
