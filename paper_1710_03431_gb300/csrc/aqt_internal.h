@@ -110,6 +110,13 @@ struct RunParams {
 constexpr int kSlotDouble2 = 3;
 constexpr int kScratchSlots = 8;
 
+// Scratch bytes of a run: the jump slots of every CTA, then, for the
+// tensor-core path, one next-step product per trajectory ([cta][TT][N] FP32
+// complex) for trajectories that jump after the rotation has read their state.
+inline size_t scratch_bytes(int n_cta, int N, int TT, bool tensor_core) {
+    return (size_t)n_cta * kScratchSlots * kSlotDouble2 * N * 16 + (tensor_core ? (size_t)n_cta * TT * N * 8 : 0);
+}
+
 // Launch the propagation (precision per aqt_precision) and the observable
 // reduction on `stream`. Returns a CUDA error code (0 on success).
 int launch_run(const RunParams &p, int precision, void *stream, size_t smem_bytes);

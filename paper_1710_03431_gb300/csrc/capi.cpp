@@ -3,10 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "aqt_internal.h"
@@ -60,6 +62,19 @@ void invalidate(aqt_ctx *c) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// f(i) for i < count on the host's cores.
+template <class F>
+void parallel_rows(size_t count, F f) {
+    const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < std::min<size_t>(nt, std::max<size_t>(count, 1)); ++t)
+        th.emplace_back([&] {
+            for (size_t i = next++; i < count; i = next++) f(i);
+        });
+    for (auto &x : th) x.join();
+}
+
 void compute_layout(aqt_ctx *c) {
     const Inputs &in = c->in;
     const size_t n = in.n, N = (size_t)1 << in.n, K = in.K;
@@ -98,7 +113,7 @@ void compute_layout(aqt_ctx *c) {
     L.jcount = take(8);
     L.obs_part = take((size_t)c->n_cta * K * 2 * 8);
     L.obs_sum = take(K * 2 * 8);
-    L.scratch = take((size_t)c->n_cta * kScratchSlots * kSlotDouble2 * N * 16);
+    L.scratch = take(scratch_bytes(c->n_cta, (int)N, c->TT, tc));
     L.status = take(4);
     L.total = off;
 }
@@ -138,7 +153,7 @@ aqt_status static_scratch_need(aqt_ctx *c, size_t *bytes) {
     compute_layout(c);
     const size_t N = (size_t)1 << c->in.n, K = c->in.K;
     const size_t part = ((size_t)c->n_cta * K * 2 * 8 + 255) & ~(size_t)255;
-    *bytes = part + (size_t)c->n_cta * kScratchSlots * kSlotDouble2 * N * 16;
+    *bytes = part + scratch_bytes(c->n_cta, (int)N, c->TT, c->in.precision == AQT_PREC_F16SPLIT);
     return AQT_OK;
 }
 
@@ -354,20 +369,21 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
         // ((a/8)*2 + k/8)*128 bytes, row a%8 at 16 bytes, column k%8 at 2 bytes.
         const size_t N = t.N, NK = N / 16, K = t.K;
         std::vector<__half> o16((K - 1) * N * N * 2);
-        for (size_t g = 0; g + 1 < K; ++g)
+        parallel_rows(K - 1, [&](size_t g) {
             for (size_t kb = 0; kb < NK; ++kb) {
                 __half *hi = &o16[((g * NK + kb) * 2) * N * 16];
                 __half *lo = hi + N * 16;
                 for (size_t a = 0; a < N; ++a)
                     for (size_t k = 0; k < 16; ++k) {
                         const double o = t.OT[g * N * N + (kb * 16 + k) * N + a];
-                        const __half h = __float2half_rn((float)o);
-                        const __half l = __float2half_rn((float)(o - (double)__half2float(h)));
+                        const __half hh = __float2half_rn((float)o);
+                        const __half ll = __float2half_rn((float)(o - (double)__half2float(hh)));
                         const size_t off = ((a >> 3) * 2 + (k >> 3)) * 64 + (a & 7) * 8 + (k & 7);
-                        hi[off] = h;
-                        lo[off] = l;
+                        hi[off] = hh;
+                        lo[off] = ll;
                     }
             }
+        });
         std::vector<float> lv(K * N * 4);
         for (size_t g = 0; g < K; ++g)
             for (size_t a = 0; a < N; ++a) {

@@ -158,6 +158,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float v[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Store two consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st2(uint32_t addr, float x, float y) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(__float_as_uint(x)),
+                 "r"(__float_as_uint(y))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
@@ -171,15 +179,15 @@ __device__ __forceinline__ void split_half(float x, __half &hi, __half &lo) {
 struct TcShared {
     // per-trajectory state (TT entries each), carved from dynamic smem
     double *ell, *logr;
-    float *x, *kinv, *P, *fscale;  // observable, 1/kappa of the stored operand, raw |D|^2, final-state scale  // 1/kappa of the stored operand, raw |D|^2, final-state scale
+    float *x, *kinv, *P, *fscale;  // observable, 1/kappa of the stored operand, raw |D|^2, final-state scale
     int *nj, *flag, *list;
-    float *red;  // [4][NC/8][16]
-    double *obs;
+    int *plist, *pcount;  // trajectories whose product this step comes from the patch buffer
+    float *red;  // [4][NC/8][16] partial sums per TMEM lane quarter
     int *count;
     volatile int *abort_flag;
-    int *epi_ok;  // the epilogue's go/stop decision for the current step, one writer
+    int *epi_ok;  // the epilogue's go/stop decision for the current wait, one writer
     uint32_t *tmem_base;
-    uint64_t *bars;  // full[4], empty[4], dfull, bready
+    uint64_t *bars;  // full[kStages], empty[kStages], dfull, bready
 };
 
 // Epilogue threads write the rows of B (levels a of this thread) for one
@@ -239,25 +247,66 @@ __device__ __forceinline__ int scatter_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
+// Next-step products y_t = O c_t of up to kSlots states held in jump slots
+// (planar FP32 real/imaginary parts), thread = level a of the products, with
+// O from the FP16 hi/lo tiles that the tensor cores use: the products the next
+// rotation would have given, had it seen these states.
+template <int MH>
+__device__ __forceinline__ void rotate_batch(const unsigned char *tile, const float *slot0, size_t slot_stride,
+                                             int nr, const int *tlist, float2 *patch, int a) {
+    constexpr int N = 128 * MH, NK = N / 16;
+    float yr[kSlots], yi[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) yr[s] = yi[s] = 0.0f;
+    const unsigned char *row = tile + (a >> 3) * 256 + (a & 7) * 16;
+#pragma unroll 4
+    for (int kh = 0; kh < 2 * NK; ++kh) {  // 8 levels b at a time: K-block kh/2, core column kh%2
+        const unsigned char *blk = row + (size_t)(kh >> 1) * N * 64 + (kh & 1) * 128;
+        uint4 w[2];
+        w[0] = *reinterpret_cast<const uint4 *>(blk);           // hi
+        w[1] = *reinterpret_cast<const uint4 *>(blk + N * 32);  // lo
+        const __half2 *hh = reinterpret_cast<const __half2 *>(w);
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 hi = __half22float2(hh[i]), lo = __half22float2(hh[4 + i]);
+            o[2 * i] = hi.x + lo.x;
+            o[2 * i + 1] = hi.y + lo.y;
+        }
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+            if (s >= nr) break;
+            const float *cre = slot0 + s * slot_stride + 8 * kh, *cim = cre + N;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                yr[s] = fmaf(o[k], cre[k], yr[s]);
+                yi[s] = fmaf(o[k], cim[k], yi[s]);
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s)
+        if (s < nr) patch[(size_t)tlist[s] * N + a] = make_float2(yr[s], yi[s]);
+}
+
 template <int MH>  // 128-level blocks of the state (N = 128 MH)
 __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16;
+    const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16, nchunk = NC / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t b_bytes = (size_t)N * NC * 2;
-    const uint32_t stage_bytes = (uint32_t)N * 64;
     unsigned char *sB_hi = smem;
     unsigned char *sB_lo = smem + b_bytes;
     unsigned char *sA = smem + 2 * b_bytes;
+    const uint32_t stage_bytes = (uint32_t)N * 64;  // one K-block of 16 levels: FP16 hi then lo, all N rows
     unsigned char *misc = sA + (size_t)kStages * stage_bytes;
     TcShared S;
-    S.bars = reinterpret_cast<uint64_t *>(misc);                      // 10 barriers
-    S.tmem_base = reinterpret_cast<uint32_t *>(misc + 96);
-    S.abort_flag = reinterpret_cast<volatile int *>(misc + 100);
-    S.count = reinterpret_cast<int *>(misc + 104);
-    S.epi_ok = reinterpret_cast<int *>(misc + 108);
-    S.obs = reinterpret_cast<double *>(misc + 112);                   // [2]
-    S.ell = reinterpret_cast<double *>(misc + 128);
+    S.bars = reinterpret_cast<uint64_t *>(misc);  // 2 kStages + 2 barriers (4 reserved)
+    S.tmem_base = reinterpret_cast<uint32_t *>(misc + 8 * (2 * kStages + 4));
+    S.abort_flag = reinterpret_cast<volatile int *>(misc + 8 * (2 * kStages + 4) + 4);
+    S.count = reinterpret_cast<int *>(misc + 8 * (2 * kStages + 4) + 8);
+    S.epi_ok = reinterpret_cast<int *>(misc + 8 * (2 * kStages + 4) + 12);
+    S.ell = reinterpret_cast<double *>(misc + 8 * (2 * kStages + 4) + 16);
     S.logr = S.ell + TT;
     S.x = reinterpret_cast<float *>(S.logr + TT);
     S.kinv = S.x + TT;
@@ -266,7 +315,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.nj = reinterpret_cast<int *>(S.fscale + TT);
     S.flag = S.nj + TT;
     S.list = S.flag + TT;
-    S.red = reinterpret_cast<float *>(S.list + TT + (TT & 1));
+    S.plist = S.list + TT;
+    S.pcount = S.plist + TT;
+    S.red = reinterpret_cast<float *>(S.pcount + 4);
 
     const uint32_t bar_full = smem_u32(S.bars), bar_empty = bar_full + 8 * kStages;
     const uint32_t bar_dfull = bar_full + 16 * kStages, bar_bready = bar_dfull + 8;
@@ -293,33 +344,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     __syncthreads();
     fence_after();
     const uint32_t tmem = *S.tmem_base;
+    const unsigned char *otab = reinterpret_cast<const unsigned char *>(p.tab.OT);
+    const size_t tile = (size_t)N * N * 4;  // one step's rotation: FP16 hi + lo
 
     if (warp == 0) {
         // ---------------- bulk-copy producer ----------------
         if (lane == 0) {
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(p.tab.OT);
             // every CTA reads the same rotation tile in each step; each warms L2 with
             // its slice of the tile one step ahead, so the ring's copies hit L2
-            const size_t tile = (size_t)NK * stage_bytes;
             const size_t piece = ((tile + p.n_cta - 1) / p.n_cta + 15) & ~(size_t)15;
             const size_t poff = (size_t)blockIdx.x * piece;
             auto warm = [&](int tg) {
                 if (tg < K - 1 && poff < tile)
-                    l2_prefetch(src + (size_t)tg * tile + poff, (uint32_t)(piece < tile - poff ? piece : tile - poff));
+                    l2_prefetch(otab + (size_t)tg * tile + poff, (uint32_t)(piece < tile - poff ? piece : tile - poff));
             };
             warm(0);
             long long it = 0;
-            for (int g = 1; g < K && !*S.abort_flag; ++g) {
+            bool run = true;
+            for (int g = 1; g < K && run && !*S.abort_flag; ++g) {
                 warm(g);
-                for (int kb = 0; kb < NK; ++kb, ++it) {
+                for (int s = 0; s < NK; ++s, ++it) {
                     const int slot = (int)(it % kStages);
-                    if (it >= kStages &&
-                        !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1), S.abort_flag, p.status,
-                                   kSiteSlot))
+                    if (it >= kStages && !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1),
+                                                    S.abort_flag, p.status, kSiteSlot)) {
+                        run = false;
                         break;
+                    }
                     mbar_expect_tx(bar_full + 8 * slot, stage_bytes);
-                    bulk_g2s(smem_u32(sA + (size_t)slot * stage_bytes),
-                             src + ((size_t)(g - 1) * NK + kb) * stage_bytes, stage_bytes, bar_full + 8 * slot);
+                    bulk_g2s(smem_u32(sA + (size_t)slot * stage_bytes), otab + (size_t)(g - 1) * tile + (size_t)s * stage_bytes,
+                             stage_bytes, bar_full + 8 * slot);
                 }
             }
             // drain: wait (bounded) for the copies still in flight
@@ -330,6 +383,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
+        // Per step, once the epilogue has written the operand (bready): K-blocks
+        // 0..NK-1, each feeding both 128-level blocks of the products; dfull tells
+        // the epilogue that all products are done.
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (0u << 7) | (0u << 10) | (0u << 15) | (1u << 16) |
                                    ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
@@ -338,15 +394,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
             long long it = 0;
             uint32_t last_bar = 0, last_par = 0;
-            for (int g = 1; g < K; ++g) {
+            bool run = true;
+            for (int g = 1; g < K && run; ++g) {
                 if (!mbar_wait(bar_bready, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteBReady)) break;
                 fence_after();
-                bool ok = true;
                 for (int kb = 0; kb < NK; ++kb, ++it) {
                     const int slot = (int)(it % kStages);
                     if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status,
                                    kSiteFull)) {
-                        ok = false;
+                        run = false;
                         break;
                     }
                     fence_after();
@@ -365,8 +421,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     last_bar = bar_empty + 8 * slot;
                     last_par = (uint32_t)((it / kStages) & 1);
                 }
-                if (!ok) break;
-                umma_commit(bar_dfull);
+                if (run) umma_commit(bar_dfull);
             }
             // on an abort, let the products already issued finish (bounded)
             // before the tensor memory is released
@@ -382,13 +437,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
         }
     } else {
-        // ---------------- epilogue (warps 2..9) ----------------
+        // ---------------- epilogue (warps 2..13) ----------------
         const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;  // ch: column group 0..2
-        const int nchunk = NC / 8;
         const int c_begin = (ch * nchunk) / 3, c_end = ((ch + 1) * nchunk) / 3;
         // jump slots: general-jump scratch (2N double2), then the FP32 state planes
         double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * kSlotDouble2 * N;
         auto slot_re = [&](int sidx) { return reinterpret_cast<float *>(scr + ((size_t)sidx * kSlotDouble2 + 2) * N); };
+        // next-step products of trajectories that jumped: [TT][N]
+        float2 *patch = reinterpret_cast<float2 *>(reinterpret_cast<double2 *>(p.scratch) +
+                                                   (size_t)p.n_cta * kSlots * kSlotDouble2 * N) +
+                        (size_t)blockIdx.x * TT * N;
         const float4 *lvl = reinterpret_cast<const float4 *>(p.tab.tclvl);
 
         // ---- initial state e_0 and the half-step after s_0 ------------------------
@@ -409,7 +467,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 S.flag[t] = 2;
             }
         }
-        if (etid == 0) *S.count = 0;
+        if (etid == 0) {
+            *S.count = 0;
+            *S.pcount = 0;
+        }
         epi_sync();
         if (etid < TT && S.flag[etid] == 1) S.list[atomicAdd(S.count, 1)] = etid;
         // B rows for all levels: level 0 holds exp(-i K_00 tau)/|.| for non-crossed
@@ -497,13 +558,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
         for (int g = 1; g < K; ++g) {
             const bool last = g == K - 1;
-            // one thread waits for the products; all epilogue threads then take
-            // the same decision (a bounded wait can expire for one thread only)
-            if (etid == 0)
-                *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
-            epi_sync();
-            if (!*S.epi_ok) break;
-            fence_after();
             const int gs = gs_next;
             float4 L[MH];
 #pragma unroll
@@ -522,65 +576,103 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
             // ---- single pass: per-trajectory sums over levels, and the next operand ----
             // D = kappa_{g-1} O c_{g-1}; the operand written now is D E^2 / kappa_{g-1}
-            // = (O c) E^2, whose norm is restored to 1 through kappa_g next step.
-            // one chunk of 8 columns: sums and the operand rows of this thread's levels
-            auto process = [&](int c, uint32_t (&r)[MH][8]) {
-                float v16[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
-                float ki[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
-#pragma unroll
-                for (int h = 0; h < MH; ++h) {
-                    const int a = 128 * h + 32 * q + lane;
-                    const float w = L[h].z, d2 = L[h].w, d2w = d2 * w;
-                    const bool in_gs = a < gs;
-                    float v[8];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
-                        const float qv = fmaf(re, re, im * im);
-                        v16[j] += qv;
-                        v16[4 + j] = fmaf(qv, w, v16[4 + j]);
-                        v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
-                        if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
-                        const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
-                        v[2 * j] = fmaf(re, fr, -im * fi);
-                        v[2 * j + 1] = fmaf(re, fi, im * fr);
-                    }
-                    if (!last) store_chunk(sB_hi, sB_lo, NC, a, c, v);
-                }
-                const float tot = reduce_scatter16(v16, lane);
-                if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
-            };
-            auto issue = [&](int c, uint32_t (&r)[MH][8]) {
-#pragma unroll
-                for (int h = 0; h < MH; ++h)
-                    tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r[h]);
-            };
-            auto settle = [&](uint32_t (&r)[MH][8]) {
-                tmem_wait();
-#pragma unroll
-                for (int h = 0; h < MH; ++h) reg_fence(r[h]);
-            };
-            // the loads of chunk c+1 are in flight while chunk c is processed
+            // = (O c) E^2, whose norm is restored to 1 through kappa_g next step. The
+            // operand is released to the next step's products before this step's jump
+            // decisions are known; a trajectory that jumps gets its next product from
+            // the patch buffer.
+            bool stop = false;
             {
-                uint32_t rA[MH][8], rB[MH][8];
-                int c = c_begin;
-                if (c < c_end) issue(c, rA);
-                settle(rA);
-                while (c < c_end) {
-                    if (c + 1 < c_end) issue(c + 1, rB);
-                    process(c, rA);
-                    settle(rB);
-                    if (++c >= c_end) break;
-                    if (c + 1 < c_end) issue(c + 1, rA);
-                    process(c, rB);
-                    settle(rA);
-                    ++c;
-                }
+                // one thread waits; all epilogue threads then take the same decision
+                // (a bounded wait can expire for one thread only)
+                if (etid == 0)
+                    *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
+                epi_sync();
+                if (!*S.epi_ok) stop = true;
             }
+            if (!stop) {
+                fence_after();
+                // trajectories that jumped last step: their products come from the patch buffer
+                if (*S.pcount > 0) {
+                    if (ch == 0) {
+                        for (int i = 0; i < *S.pcount; ++i) {
+                            const int t = S.plist[i];
+#pragma unroll
+                            for (int h = 0; h < MH; ++h) {
+                                const float2 y = patch[(size_t)t * N + 128 * h + 32 * q + lane];
+                                tmem_st2(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 2 * t), y.x, y.y);
+                            }
+                        }
+                        tmem_st_wait();
+                    }
+                    fence_before();
+                    epi_sync();
+                    fence_after();
+                    if (etid == 0) *S.pcount = 0;
+                }
+                // one chunk of 8 columns: sums and the operand rows of this thread's levels
+                auto process = [&](int c, uint32_t (&r)[MH][8]) {
+                    float v16[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
+                    float ki[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
+#pragma unroll
+                    for (int h = 0; h < MH; ++h) {
+                        const int a = 128 * h + 32 * q + lane;
+                        const float w = L[h].z, d2 = L[h].w, d2w = d2 * w;
+                        const bool in_gs = a < gs;
+                        float v[8];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
+                            const float qv = fmaf(re, re, im * im);
+                            v16[j] += qv;
+                            v16[4 + j] = fmaf(qv, w, v16[4 + j]);
+                            v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
+                            if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
+                            const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
+                            v[2 * j] = fmaf(re, fr, -im * fi);
+                            v[2 * j + 1] = fmaf(re, fi, im * fr);
+                        }
+                        if (!last) store_chunk(sB_hi, sB_lo, NC, a, c, v);
+                    }
+                    const float tot = reduce_scatter16(v16, lane);
+                    if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+                };
+                auto issue = [&](int c, uint32_t (&r)[MH][8]) {
+#pragma unroll
+                    for (int h = 0; h < MH; ++h)
+                        tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r[h]);
+                };
+                auto settle = [&](uint32_t (&r)[MH][8]) {
+                    tmem_wait();
+#pragma unroll
+                    for (int h = 0; h < MH; ++h) reg_fence(r[h]);
+                };
+                // the loads of chunk c+1 are in flight while chunk c is processed
+                {
+                    uint32_t rA[MH][8], rB[MH][8];
+                    int c = c_begin;
+                    if (c < c_end) issue(c, rA);
+                    settle(rA);
+                    while (c < c_end) {
+                        if (c + 1 < c_end) issue(c + 1, rB);
+                        process(c, rA);
+                        settle(rB);
+                        if (++c >= c_end) break;
+                        if (c + 1 < c_end) issue(c + 1, rA);
+                        process(c, rB);
+                        settle(rA);
+                        ++c;
+                    }
+                }
+                // the operand is written and the products read: the next step may start
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                mbar_arrive(bar_bready);
+            }
+            if (stop) break;
             if (etid == 0) *S.count = 0;
             epi_sync();
             // ---- per trajectory: clock, crossings, next kappa, observable -------------------
@@ -637,7 +729,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         for (int j = 0; j < 4; ++j) {
                             const int t = 4 * c + j;
                             if (S.flag[t] != 0) continue;
-                            const float sc = S.fscale[t], re = d[2 * j], im = d[2 * j + 1];
+                            const float re = d[2 * j], im = d[2 * j + 1];
+                            const float sc = S.fscale[t];
                             double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
                             fs[0] = (re * e2r[h] - im * e2i[h]) * sc;
                             fs[1] = (re * e2i[h] + im * e2r[h]) * sc;
@@ -649,16 +742,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             for (int base = 0; base < ncross; base += kSlots) {
                 const int nr = min(kSlots, ncross - base);
                 if (ch == 0) {
+                    // the state after the rotation of this step, normalised later: from the
+                    // products (last step) or from the operand written above, D = B / E^2
                     for (int sidx = 0; sidx < nr; ++sidx) {
                         const int t = S.list[base + sidx];
-                        const double inv = 1.0 / sqrt((double)S.P[t]);
                         const int c = t >> 2, j = t & 3;
                         for (int h = 0; h < MH; ++h) {
                             const int a = 128 * h + 32 * q + lane;
-                            float d[8];
-                            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
-                            slot_re(sidx)[a] = d[2 * j] * inv;
-                            slot_re(sidx)[N + a] = d[2 * j + 1] * inv;
+                            float re, im;
+                            if (last) {
+                                float d[8];
+                                tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), d);
+                                re = d[2 * j];
+                                im = d[2 * j + 1];
+                            } else {
+                                const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16 + j * 4;
+                                const __half2 bh = *reinterpret_cast<const __half2 *>(sB_hi + off);
+                                const __half2 bl = *reinterpret_cast<const __half2 *>(sB_lo + off);
+                                const float br = __low2float(bh) + __low2float(bl);
+                                const float bi = __high2float(bh) + __high2float(bl);
+                                const float m = 1.0f / (e2r[h] * e2r[h] + e2i[h] * e2i[h]);
+                                re = (br * e2r[h] + bi * e2i[h]) * m;
+                                im = (bi * e2r[h] - br * e2i[h]) * m;
+                            }
+                            slot_re(sidx)[a] = re;
+                            slot_re(sidx)[N + a] = im;
                         }
                     }
                 }
@@ -681,21 +789,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         S.nj[t] = nj;
                         S.x[t] = (float)xs;
                         S.kinv[t] = 1.0f;
+                        if (!last) S.plist[atomicAdd(S.pcount, 1)] = t;
                     }
                 }
                 epi_sync();
-                for (int sidx = 0; sidx < nr && ch == 0; ++sidx) {
+                // next step's products of the new states (the rotation already ran on the old ones)
+                if (!last && etid < N)
+                    rotate_batch<MH>(otab + (size_t)g * tile, slot_re(0), (size_t)kSlotDouble2 * N * 4, nr,
+                                     S.list + base, patch, etid);
+                for (int sidx = 0; sidx < nr && ch == 0 && last; ++sidx) {
                     const int t = S.list[base + sidx];
                     for (int h = 0; h < MH; ++h) {
                         const int a = 128 * h + 32 * q + lane;
-                        const float vr = slot_re(sidx)[a], vi = slot_re(sidx)[N + a];
-                        if (!last) {
-                            store_one(sB_hi, sB_lo, NC, a, t, vr, vi);
-                        } else {
-                            double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
-                            fs[0] = vr;
-                            fs[1] = vi;
-                        }
+                        double *fs = p.final_state + ((size_t)(t0 + t) * N + a) * 2;
+                        fs[0] = slot_re(sidx)[a];
+                        fs[1] = slot_re(sidx)[N + a];
                     }
                 }
                 epi_sync();
@@ -717,9 +825,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = sx2;
                 }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fence_before();
-            mbar_arrive(bar_bready);
         }
     }
     fence_before();
@@ -731,9 +836,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
 }  // namespace
 
 size_t tc_smem_bytes(int N, int TT) {
-    const int NC = 2 * TT;
+    const int NC = 2 * TT, nchunk = NC / 8;
     size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
-    b += 128 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 3) + 16 + (size_t)4 * (NC / 8) * 16 * 4;
+    b += 8 * (2 * kStages + 4) + 16 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 4) + 16 +
+         (size_t)4 * nchunk * 16 * 4;
     b = (b + 1023) & ~(size_t)1023;
     // one CTA per SM: the kernel allocates tensor-memory columns without sharing
     return b < 120 * 1024 ? 120 * 1024 : b;
