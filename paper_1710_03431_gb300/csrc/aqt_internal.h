@@ -80,6 +80,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
 struct DevTables {
     const double *kdiag, *ehalf, *d2, *G, *lvlE;
     const void *Rt;     // [g][alpha][b][a]: double (FP64 path) or float
+    const float *Gt32;  // FP32 and tensor-core paths: [g][b][8] stage-one rates, alpha padded to 8
     const float *ehalf32;
     const int32_t *mfirst, *msize;
     const GridMeta *meta;

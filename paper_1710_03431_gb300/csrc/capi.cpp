@@ -16,7 +16,7 @@
 using namespace aqt;
 
 struct Layout {
-    size_t kdiag, ehalf, ehalf32, d2, G, R, lvlE, mfirst, msize, meta, OT, tclvl;
+    size_t kdiag, ehalf, ehalf32, d2, G, Gt, R, lvlE, mfirst, msize, meta, OT, tclvl;
     size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, total;
 };
 
@@ -101,6 +101,7 @@ void compute_layout(aqt_ctx *c) {
     L.ehalf32 = take(K * N * 2 * 4);
     L.d2 = take(K * N * 8);
     L.G = take(K * n * N * 8);
+    L.Gt = take(in.precision == AQT_PREC_FP64 ? 0 : K * N * 8 * 4);
     L.R = take(K * n * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
     L.lvlE = take(K * N * 8);
     L.mfirst = take(K * N * 4);
@@ -183,6 +184,7 @@ aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
     p->tab.d2 = (const double *)(c->ws + L.d2);
     p->tab.G = (const double *)(c->ws + L.G);
     p->tab.Rt = c->ws + L.R;
+    p->tab.Gt32 = (const float *)(c->ws + L.Gt);
     p->tab.lvlE = (const double *)(c->ws + L.lvlE);
     p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p->tab.msize = (const int32_t *)(c->ws + L.msize);
@@ -356,6 +358,16 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     if (!e) e = put(L.G, t.G.data(), t.G.size() * 8);
     if (!e && !t.Rt.empty()) e = put(L.R, t.Rt.data(), t.Rt.size() * 8);
     if (!e && !t.Rt32.empty()) e = put(L.R, t.Rt32.data(), t.Rt32.size() * 4);
+    std::vector<float> gt;
+    if (c->in.precision != AQT_PREC_FP64) {
+        // stage-one rates level-major in FP32, 8 alphas per level (zero past n)
+        const size_t N = t.N, n = t.n, K = t.K;
+        gt.assign(K * N * 8, 0.0f);
+        for (size_t g = 0; g < K; ++g)
+            for (size_t al = 0; al < n; ++al)
+                for (size_t b = 0; b < N; ++b) gt[(g * N + b) * 8 + al] = (float)t.G[(g * n + al) * N + b];
+        if (!e) e = put(L.Gt, gt.data(), gt.size() * 4);
+    }
     if (!e) e = put(L.lvlE, t.lvlE.data(), t.lvlE.size() * 8);
     if (!e) e = put(L.mfirst, t.mfirst.data(), t.mfirst.size() * 4);
     if (!e) e = put(L.msize, t.msize.data(), t.msize.size() * 4);
@@ -437,6 +449,7 @@ aqt_status aqt_run(aqt_ctx *c, void *stream) {
     p.tab.d2 = (const double *)(c->ws + L.d2);
     p.tab.G = (const double *)(c->ws + L.G);
     p.tab.Rt = c->ws + L.R;
+    p.tab.Gt32 = (const float *)(c->ws + L.Gt);
     p.tab.lvlE = (const double *)(c->ws + L.lvlE);
     p.tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
     p.tab.msize = (const int32_t *)(c->ws + L.msize);

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "aqt_internal.h"
 #include "philox.cuh"
@@ -427,32 +428,74 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
             T qv[NPL];
 #pragma unroll
             for (int j = 0; j < NPL; ++j) qv[j] = cr[j] * cr[j] + ci[j] * ci[j];
-            // stage one over units (alpha, b) in that order. The total rate is
-            // sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2 2 Im K_bb, so the
-            // walk over alpha stops at the first alpha whose cumulative sum passes
-            // the target, one warp sum per alpha visited.
+            // stage one over units (alpha, b) in that order
             T total = T(0);
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2(j);
-            total = warp_sum(total);
-            const T target = (T)u1 * total;
             T cum = T(0), cum_last = T(0);
             int last = -1;
-            for (int a_ = 0; a_ < n && al < 0; ++a_) {
-                T acc = T(0);
+            if constexpr (std::is_same<T, float>::value) {
+                // all per-alpha totals in one pass over the level-major FP32 rates
+                // (8 alphas per level, two float4)
+                const float4 *gt = reinterpret_cast<const float4 *>(p.tab.Gt32) + (size_t)g * N * 2;
+                float S8[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) S8[k] = 0.0f;
 #pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int b = 32 * j + lane;
-                    if (b < N) acc += qv[j] * (T)Gg[(size_t)a_ * N + b];
+                    if (b < N) {
+                        const float4 x = gt[2 * b], y = gt[2 * b + 1];
+                        S8[0] = fmaf(qv[j], x.x, S8[0]);
+                        S8[1] = fmaf(qv[j], x.y, S8[1]);
+                        S8[2] = fmaf(qv[j], x.z, S8[2]);
+                        S8[3] = fmaf(qv[j], x.w, S8[3]);
+                        S8[4] = fmaf(qv[j], y.x, S8[4]);
+                        S8[5] = fmaf(qv[j], y.y, S8[5]);
+                        S8[6] = fmaf(qv[j], y.z, S8[6]);
+                        S8[7] = fmaf(qv[j], y.w, S8[7]);
+                    }
                 }
-                acc = warp_sum(acc);
-                if (acc > T(0)) {
-                    last = a_;
-                    cum_last = cum;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) S8[k] += __shfl_xor_sync(0xffffffffu, S8[k], o);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) total += S8[k];
+                const T target = (T)u1 * total;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (al < 0 && k < n) {
+                        if (S8[k] > 0.0f) {
+                            last = k;
+                            cum_last = cum;
+                        }
+                        if (S8[k] > 0.0f && cum + S8[k] > target) al = k;
+                        else cum += S8[k];
+                    }
+            } else {
+                // The total rate is sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2
+                // 2 Im K_bb, so the walk over alpha stops at the first alpha whose
+                // cumulative sum passes the target, one warp sum per alpha visited.
+#pragma unroll
+                for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2(j);
+                total = warp_sum(total);
+                const T target = (T)u1 * total;
+                for (int a_ = 0; a_ < n && al < 0; ++a_) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int j = 0; j < NPL; ++j) {
+                        const int b = 32 * j + lane;
+                        if (b < N) acc += qv[j] * (T)Gg[(size_t)a_ * N + b];
+                    }
+                    acc = warp_sum(acc);
+                    if (acc > T(0)) {
+                        last = a_;
+                        cum_last = cum;
+                    }
+                    if (acc > T(0) && cum + acc > target) al = a_;
+                    else cum += acc;
                 }
-                if (acc > T(0) && cum + acc > target) al = a_;
-                else cum += acc;
             }
+            const T target = (T)u1 * total;
             if (al < 0) {  // rounding at the top of the distribution
                 al = last;
                 cum = cum_last;

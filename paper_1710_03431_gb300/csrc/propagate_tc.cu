@@ -8,16 +8,23 @@
 //   O C ~ O_hi C_hi + O_hi C_lo + O_lo C_hi   (hi = fp16(x), lo = fp16(x - hi)),
 // a 22-bit-mantissa product. Roles (one CTA per SM, persistent over the grid):
 //   warp 0  streams O_hi/O_lo K-blocks (16 levels) into a 4-stage shared-memory
-//           ring with bulk copies (cp.async.bulk, mbarrier transaction counts);
+//           ring with bulk copies (cp.async.bulk, mbarrier transaction counts)
+//           and warms L2 with its slice of the next step's rotation tile;
 //   warp 1  owns the tensor memory and issues tcgen05.mma from one lane;
-//   warps 2-13 are the epilogue (3 column groups x 4 TMEM lane quarters): read D from tensor memory, form per-trajectory
-//           norms and decay sums (cross-lane reductions), take both frozen
-//           half-steps around s_g with the exact diagonal factors, test the
-//           norm-threshold jump clock in FP64, accumulate the observable, and
-//           write the next step's C_hi/C_lo operand back into shared memory.
-// Trajectories whose clock crosses its threshold are handed to the same jump
-// resolution as the SIMT kernel (App. C; App. B.1, Eq. Pi(t); Eq. jump), one
-// epilogue warp per trajectory, state in registers.
+//   warps 2-13 are the epilogue (3 column groups x 4 TMEM lane quarters).
+// Per step the epilogue (1) waits for the products D, (2) in one pass turns D
+// into the next operand C = D E^2 / kappa_{g-1} (both frozen half-steps around
+// s_g with their exact diagonal factors, normalisation deferred by one step)
+// and releases it to the next rotation at once, then, while that rotation
+// runs, (3) recomputes the per-trajectory norms and decay sums from the
+// operand it wrote (cross-lane reductions), advances the FP64 jump clocks,
+// finds crossings and records the observable. A trajectory whose clock
+// crosses its threshold is resolved by one epilogue warp with the same
+// register routine as the SIMT kernel (App. C; App. B.1, Eq. Pi(t);
+// Eq. jump); since the rotation already ran on its old state, the epilogue
+// computes the product of its new state (FP32 over the same FP16 hi/lo
+// tiles) and writes it into tensor memory before the next pass (2). At the
+// last grid point there is no next rotation and the sums come from D.
 //
 // Operand layouts (no swizzle, 8x16-byte core matrices):
 //   A = O block [N rows][16 cols], K-major: core (r/8, k/8) at ((r/8)*2 + k/8)*128 B
@@ -392,6 +399,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const uint32_t a_lbo = 128, a_sbo = 256;
             const uint32_t b_lbo = (uint32_t)NC * 16, b_sbo = 128;
             const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
+            // ring slot 0 (A, hi half, block h = 0) and K-block 0 (B): every other
+            // operand is these plus a byte offset (shared-memory addresses < 256 KB
+            // keep the 14-bit address field from overflowing)
+            const uint64_t dA = umma_desc(smem_u32(sA), a_lbo, a_sbo);
+            const uint64_t dBh = umma_desc(bhi, b_lbo, b_sbo), dBl = umma_desc(blo, b_lbo, b_sbo);
+            uint32_t dcol[MH];
+#pragma unroll
+            for (int h = 0; h < MH; ++h) dcol[h] = tmem + (uint32_t)(h * NC);
             long long it = 0;
             uint32_t last_bar = 0, last_par = 0;
             bool run = true;
@@ -406,16 +421,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         break;
                     }
                     fence_after();
-                    const uint32_t a0 = smem_u32(sA + (size_t)slot * stage_bytes);
+                    // descriptors advance by (byte offset >> 4) in their address field
+                    const uint64_t a0 = dA + ((uint64_t)slot * stage_bytes >> 4);
+                    const uint64_t bk = (uint64_t)kb * NC * 2;  // kb * NC * 32 bytes
+#pragma unroll
                     for (int h = 0; h < MH; ++h) {
-                        const uint32_t d = tmem + (uint32_t)(h * NC);
-                        const uint64_t ahi = umma_desc(a0 + h * 4096, a_lbo, a_sbo);
-                        const uint64_t alo = umma_desc(a0 + (uint32_t)N * 32 + h * 4096, a_lbo, a_sbo);
-                        const uint64_t bh = umma_desc(bhi + (uint32_t)kb * NC * 32, b_lbo, b_sbo);
-                        const uint64_t bl = umma_desc(blo + (uint32_t)kb * NC * 32, b_lbo, b_sbo);
-                        umma_f16(d, ahi, bh, idesc, kb > 0 ? 1u : 0u);
-                        umma_f16(d, ahi, bl, idesc, 1u);
-                        umma_f16(d, alo, bh, idesc, 1u);
+                        const uint64_t ahi = a0 + (uint64_t)h * 256, alo = ahi + (uint64_t)N * 2;
+                        umma_f16(dcol[h], ahi, dBh + bk, idesc, kb > 0 ? 1u : 0u);
+                        umma_f16(dcol[h], ahi, dBl + bk, idesc, 1u);
+                        umma_f16(dcol[h], alo, dBh + bk, idesc, 1u);
                     }
                     umma_commit(bar_empty + 8 * slot);
                     last_bar = bar_empty + 8 * slot;
@@ -609,33 +623,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     fence_after();
                     if (etid == 0) *S.pcount = 0;
                 }
-                // one chunk of 8 columns: sums and the operand rows of this thread's levels
+                // one chunk of 8 columns: the operand rows of this thread's levels and, at
+                // the last grid point (no next rotation), the sums over levels
                 auto process = [&](int c, uint32_t (&r)[MH][8]) {
-                    float v16[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
                     float ki[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
+                    if (!last) {
+#pragma unroll
+                        for (int h = 0; h < MH; ++h) {
+                            float v[8];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
+                                const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
+                                v[2 * j] = fmaf(re, fr, -im * fi);
+                                v[2 * j + 1] = fmaf(re, fi, im * fr);
+                            }
+                            store_chunk(sB_hi, sB_lo, NC, 128 * h + 32 * q + lane, c, v);
+                        }
+                        return;
+                    }
+                    float v16[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
 #pragma unroll
                     for (int h = 0; h < MH; ++h) {
                         const int a = 128 * h + 32 * q + lane;
-                        const float w = L[h].z, d2 = L[h].w, d2w = d2 * w;
+                        const float w = L[h].z, d2 = L[h].w;
                         const bool in_gs = a < gs;
-                        float v[8];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
-                            const float qv = fmaf(re, re, im * im);
+                            // |D|^2 kinv^2: the scale of the operand rows written in the other form
+                            const float qv = fmaf(re, re, im * im) * ki[j] * ki[j];
                             v16[j] += qv;
                             v16[4 + j] = fmaf(qv, w, v16[4 + j]);
-                            v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
                             if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
-                            const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
-                            v[2 * j] = fmaf(re, fr, -im * fi);
-                            v[2 * j + 1] = fmaf(re, fi, im * fr);
                         }
-                        if (!last) store_chunk(sB_hi, sB_lo, NC, a, c, v);
                     }
                     const float tot = reduce_scatter16(v16, lane);
                     if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
@@ -673,6 +698,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 mbar_arrive(bar_bready);
             }
             if (stop) break;
+            // ---- sums over levels from the operand just written (B = D E^2 kinv), while the
+            // next rotation runs: |D|^2 kinv^2 = |B|^2 / |E^2|^2 with |E^2|^2 = d2^2 ----------
+            if (!last) {
+                for (int c = c_begin; c < c_end; ++c) {
+                    float v16[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
+#pragma unroll
+                    for (int h = 0; h < MH; ++h) {
+                        const int a = 128 * h + 32 * q + lane;
+                        const float w = L[h].z, d2 = L[h].w, d2w = d2 * w, ie = 1.0f / (d2 * d2);
+                        const bool in_gs = a < gs;
+                        const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
+                        uint4 bw[2];
+                        bw[0] = *reinterpret_cast<const uint4 *>(sB_hi + off);
+                        bw[1] = *reinterpret_cast<const uint4 *>(sB_lo + off);
+                        const __half2 *bh = reinterpret_cast<const __half2 *>(bw);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 hi = __half22float2(bh[j]), lo = __half22float2(bh[4 + j]);
+                            const float br = hi.x + lo.x, bi = hi.y + lo.y;
+                            const float qv = fmaf(br, br, bi * bi) * ie;
+                            v16[j] += qv;
+                            v16[4 + j] = fmaf(qv, w, v16[4 + j]);
+                            v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
+                            if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
+                        }
+                    }
+                    const float tot = reduce_scatter16(v16, lane);
+                    if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+                }
+            }
             if (etid == 0) *S.count = 0;
             epi_sync();
             // ---- per trajectory: clock, crossings, next kappa, observable -------------------
@@ -707,10 +764,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         S.flag[t] = 0;
                         S.ell[t] = last ? lB : lA;
                         S.x[t] = X / nB;
+                        // kappa_g^2 = |O c|^2 (1 - dB)(1 - dA) with |O c|^2 = P (the sums are of
+                        // |D|^2 kinv_{g-1}^2)
                         const float ko = S.kinv[t];
-                        // kappa_g^2 = |O c|^2 (1 - dB)(1 - dA) with |O c|^2 = P kinv_{g-1}^2
-                        S.kinv[t] = rsqrtf(Pt * ko * ko * (1.0f - dB) * (1.0f - dA));
-                        S.fscale[t] = rsqrtf(nB);
+                        S.kinv[t] = rsqrtf(Pt * (1.0f - dB) * (1.0f - dA));
+                        // final-state scale at the last grid point: 1/|D E| = kinv_{g-1} / sqrt(nB)
+                        S.fscale[t] = ko * rsqrtf(nB);
                     } else {
                         S.flag[t] = 1;
                         S.list[atomicAdd(S.count, 1)] = t;
