@@ -505,7 +505,10 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
 #pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int b = 32 * j + lane;
-                    w[j] = b < N ? qv[j] * (T)Gg[(size_t)al * N + b] : T(0);
+                    if constexpr (std::is_same<T, float>::value)
+                        w[j] = b < N ? qv[j] * p.tab.Gt32[((size_t)g * N + b) * 8 + al] : 0.0f;  // cached by stage one
+                    else
+                        w[j] = b < N ? qv[j] * (T)Gg[(size_t)al * N + b] : T(0);
                 }
                 bsrc = reg_pick(w, target - cum, lane);
             }

@@ -189,6 +189,7 @@ struct TcShared {
     float *x, *kinv, *P, *fscale;  // observable, 1/kappa of the stored operand, raw |D|^2, final-state scale
     int *nj, *flag, *list;
     int *plist, *pcount;  // trajectories whose product this step comes from the patch buffer
+    float2 *cst;          // [N] one jumped state staged for its next-step product
     float *red;  // [4][NC/8][16] partial sums per TMEM lane quarter
     int *count;
     volatile int *abort_flag;
@@ -254,46 +255,33 @@ __device__ __forceinline__ int scatter_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-// Next-step products y_t = O c_t of up to kSlots states held in jump slots
-// (planar FP32 real/imaginary parts), thread = level a of the products, with
-// O from the FP16 hi/lo tiles that the tensor cores use: the products the next
-// rotation would have given, had it seen these states.
+// Next-step product y = O c of one state staged in shared memory (cs[b] =
+// (re, im), N levels), thread = level a of the product, with O from the FP16
+// hi/lo tiles that the tensor cores use: the product the next rotation would
+// have given, had it seen this state.
 template <int MH>
-__device__ __forceinline__ void rotate_batch(const unsigned char *tile, const float *slot0, size_t slot_stride,
-                                             int nr, const int *tlist, float2 *patch, int a) {
+__device__ __forceinline__ float2 rotate_row(const unsigned char *tile, const float2 *cs, int a) {
     constexpr int N = 128 * MH, NK = N / 16;
-    float yr[kSlots], yi[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) yr[s] = yi[s] = 0.0f;
+    float yr = 0.0f, yi = 0.0f;
     const unsigned char *row = tile + (a >> 3) * 256 + (a & 7) * 16;
-#pragma unroll 4
+#pragma unroll 8
     for (int kh = 0; kh < 2 * NK; ++kh) {  // 8 levels b at a time: K-block kh/2, core column kh%2
         const unsigned char *blk = row + (size_t)(kh >> 1) * N * 64 + (kh & 1) * 128;
         uint4 w[2];
         w[0] = *reinterpret_cast<const uint4 *>(blk);           // hi
         w[1] = *reinterpret_cast<const uint4 *>(blk + N * 32);  // lo
         const __half2 *hh = reinterpret_cast<const __half2 *>(w);
-        float o[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const float2 hi = __half22float2(hh[i]), lo = __half22float2(hh[4 + i]);
-            o[2 * i] = hi.x + lo.x;
-            o[2 * i + 1] = hi.y + lo.y;
-        }
-#pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
-            if (s >= nr) break;
-            const float *cre = slot0 + s * slot_stride + 8 * kh, *cim = cre + N;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                yr[s] = fmaf(o[k], cre[k], yr[s]);
-                yi[s] = fmaf(o[k], cim[k], yi[s]);
-            }
+            const float2 c0 = cs[8 * kh + 2 * i], c1 = cs[8 * kh + 2 * i + 1];
+            yr = fmaf(hi.x + lo.x, c0.x, yr);
+            yi = fmaf(hi.x + lo.x, c0.y, yi);
+            yr = fmaf(hi.y + lo.y, c1.x, yr);
+            yi = fmaf(hi.y + lo.y, c1.y, yi);
         }
     }
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s)
-        if (s < nr) patch[(size_t)tlist[s] * N + a] = make_float2(yr[s], yi[s]);
+    return make_float2(yr, yi);
 }
 
 template <int MH>  // 128-level blocks of the state (N = 128 MH)
@@ -324,7 +312,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.list = S.flag + TT;
     S.plist = S.list + TT;
     S.pcount = S.plist + TT;
-    S.red = reinterpret_cast<float *>(S.pcount + 4);
+    S.cst = reinterpret_cast<float2 *>(S.pcount + 4);
+    S.red = reinterpret_cast<float *>(S.cst + N);
 
     const uint32_t bar_full = smem_u32(S.bars), bar_empty = bar_full + 8 * kStages;
     const uint32_t bar_dfull = bar_full + 16 * kStages, bar_bready = bar_dfull + 8;
@@ -853,9 +842,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 }
                 epi_sync();
                 // next step's products of the new states (the rotation already ran on the old ones)
-                if (!last && etid < N)
-                    rotate_batch<MH>(otab + (size_t)g * tile, slot_re(0), (size_t)kSlotDouble2 * N * 4, nr,
-                                     S.list + base, patch, etid);
+                for (int sidx = 0; sidx < nr && !last; ++sidx) {
+                    if (etid < N) S.cst[etid] = make_float2(slot_re(sidx)[etid], slot_re(sidx)[N + etid]);
+                    epi_sync();
+                    if (etid < N)
+                        patch[(size_t)S.list[base + sidx] * N + etid] = rotate_row<MH>(otab + (size_t)g * tile, S.cst, etid);
+                    epi_sync();
+                }
                 for (int sidx = 0; sidx < nr && ch == 0 && last; ++sidx) {
                     const int t = S.list[base + sidx];
                     for (int h = 0; h < MH; ++h) {
@@ -898,7 +891,7 @@ size_t tc_smem_bytes(int N, int TT) {
     const int NC = 2 * TT, nchunk = NC / 8;
     size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
     b += 8 * (2 * kStages + 4) + 16 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 4) + 16 +
-         (size_t)4 * nchunk * 16 * 4;
+         (size_t)4 * nchunk * 16 * 4 + (size_t)N * 8;
     b = (b + 1023) & ~(size_t)1023;
     // one CTA per SM: the kernel allocates tensor-memory columns without sharing
     return b < 120 * 1024 ? 120 * 1024 : b;
