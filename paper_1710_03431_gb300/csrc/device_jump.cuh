@@ -320,10 +320,12 @@ static __device__ int general_draw_apply(const RunParams &p, int g, double u1, d
 // not); on return, the normalised state at the end of the half-step. ell,
 // logr, nj: the trajectory's clock, log threshold and jump count (the same on
 // every lane). slow: 2N double2 of per-warp scratch for the general jump.
+// klev (FP32 paths, optional): (Re K_aa, 2 Im K_aa) of grid point g staged in
+// shared memory; otherwise the FP64 table is read.
 template <typename T, int NPL>
 static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g, int half, int64_t traj, T *sre,
                                                       T *sim, int stride, double &ell, double &logr, int &nj,
-                                                      int lane, double2 *slow) {
+                                                      int lane, double2 *slow, const float2 *klev = nullptr) {
     const int N = p.N, n = p.n;
     const GridMeta meta = p.tab.meta[g];
     const double *kd = p.tab.kdiag + (size_t)g * N * 2;
@@ -342,10 +344,14 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     // keep registers free
     auto kre = [&](int j) -> T {
         const int a = 32 * j + lane;
+        if constexpr (std::is_same<T, float>::value)
+            if (klev) return a < N ? klev[a].x : 0.0f;
         return a < N ? (T)kd[2 * a] : T(0);
     };
     auto kim2 = [&](int j) -> T {
         const int a = 32 * j + lane;
+        if constexpr (std::is_same<T, float>::value)
+            if (klev) return a < N ? klev[a].y : 0.0f;
         return a < N ? (T)(2.0 * kd[2 * a + 1]) : T(0);
     };
     // c <- c exp(-i K t) / |.|; false if the norm is not positive and finite

@@ -789,6 +789,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const int ncross = *S.count;
             for (int base = 0; base < ncross; base += kSlots) {
                 const int nr = min(kSlots, ncross - base);
+                // the diagonal of K at s_g for the resolving warps (both half-steps)
+                if (etid < N) {
+                    const double *kd = p.tab.kdiag + (size_t)g * N * 2;
+                    S.cst[etid] = make_float2((float)kd[2 * etid], (float)(2.0 * kd[2 * etid + 1]));
+                }
                 if (ch == 0) {
                     // the state after the rotation of this step, normalised later: from the
                     // products (last step) or from the operand written above, D = B / E^2
@@ -825,12 +830,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     int nj = S.nj[t];
                     float *sre = slot_re(e);
                     double2 *slow = scr + (size_t)e * kSlotDouble2 * N;
-                    jump_half_step<float, 4 * MH>(p, g, 0, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow);
+                    jump_half_step<float, 4 * MH>(p, g, 0, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow, S.cst);
                     double xs = 0.0;
                     for (int a = lane; a < gs; a += 32) xs += (double)sre[a] * sre[a] + (double)sre[N + a] * sre[N + a];
                     xs = warp_sum(xs);
                     if (!last)
-                        jump_half_step<float, 4 * MH>(p, g, 1, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow);
+                        jump_half_step<float, 4 * MH>(p, g, 1, t0 + t, sre, sre + N, 1, el, lr, nj, lane, slow, S.cst);
                     if (lane == 0) {
                         S.ell[t] = el;
                         S.logr[t] = lr;
