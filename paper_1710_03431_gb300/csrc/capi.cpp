@@ -376,25 +376,29 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
         if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
         if (!e) e = cudaStreamSynchronize(st);
     } else if (c->in.precision == AQT_PREC_F16SPLIT) {
-        // A-operand tiles: per grid step and K-block of 16 levels b, the hi then
-        // lo halves of O[a][b] in 8x16-byte core matrices, core (a/8, k/8) at
-        // ((a/8)*2 + k/8)*128 bytes, row a%8 at 16 bytes, column k%8 at 2 bytes.
-        const size_t N = t.N, NK = N / 16, K = t.K;
+        // A-operand tiles in the order the tensor-core kernel streams them: per grid
+        // step, 128-level block h of rows a, and pair of K-blocks (16 levels b
+        // each), a 16 KB stage: the hi halves of O[a][b] for the two K-blocks
+        // (4 KB each), then the lo halves. Each 4 KB block holds 8x16-byte core
+        // matrices: core (a/8, k/8) at ((a/8)*2 + k/8)*128 bytes, row a%8 at 16
+        // bytes, column k%8 at 2 bytes (a, k local to the block).
+        const size_t N = t.N, NK = N / 16, K = t.K, MH = N / 128;
         std::vector<__half> o16((K - 1) * N * N * 2);
         parallel_rows(K - 1, [&](size_t g) {
-            for (size_t kb = 0; kb < NK; ++kb) {
-                __half *hi = &o16[((g * NK + kb) * 2) * N * 16];
-                __half *lo = hi + N * 16;
-                for (size_t a = 0; a < N; ++a)
-                    for (size_t k = 0; k < 16; ++k) {
-                        const double o = t.OT[g * N * N + (kb * 16 + k) * N + a];
-                        const __half hh = __float2half_rn((float)o);
-                        const __half ll = __float2half_rn((float)(o - (double)__half2float(hh)));
-                        const size_t off = ((a >> 3) * 2 + (k >> 3)) * 64 + (a & 7) * 8 + (k & 7);
-                        hi[off] = hh;
-                        lo[off] = ll;
-                    }
-            }
+            for (size_t h = 0; h < MH; ++h)
+                for (size_t kb = 0; kb < NK; ++kb) {
+                    __half *hi = &o16[((g * MH + h) * (NK / 2) + kb / 2) * 8192 + (kb & 1) * 2048];
+                    __half *lo = hi + 4096;
+                    for (size_t al = 0; al < 128; ++al)
+                        for (size_t k = 0; k < 16; ++k) {
+                            const double o = t.OT[g * N * N + (kb * 16 + k) * N + 128 * h + al];
+                            const __half hh = __float2half_rn((float)o);
+                            const __half ll = __float2half_rn((float)(o - (double)__half2float(hh)));
+                            const size_t off = ((al >> 3) * 2 + (k >> 3)) * 64 + (al & 7) * 8 + (k & 7);
+                            hi[off] = hh;
+                            lo[off] = ll;
+                        }
+                }
         });
         std::vector<float> lv(K * N * 4);
         for (size_t g = 0; g < K; ++g)

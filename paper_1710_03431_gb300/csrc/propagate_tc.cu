@@ -53,6 +53,9 @@ constexpr int kEpiWarps = 12;                       // 3 column groups x 4 TMEM 
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kTcThreads = 64 + kEpiThreads;
 constexpr int kStages = 4;
+// One ring stage: 128 rows (block h of the product) x 2 K-blocks of 16 levels
+// of O, FP16 hi (two 4 KB blocks) then lo (two 4 KB blocks).
+constexpr uint32_t kStageBytes = 16384;
 constexpr int kSlots = kScratchSlots;
 constexpr long long kWaitLimit = 1ll << 22;           // polls, and
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait (~1 ms)
@@ -195,7 +198,7 @@ struct TcShared {
     volatile int *abort_flag;
     int *epi_ok;  // the epilogue's go/stop decision for the current wait, one writer
     uint32_t *tmem_base;
-    uint64_t *bars;  // full[kStages], empty[kStages], dfull, bready
+    uint64_t *bars;  // full[kStages], empty[kStages], dfull, rowsA, rowsB
 };
 
 // Epilogue threads write the rows of B (levels a of this thread) for one
@@ -263,13 +266,15 @@ template <int MH>
 __device__ __forceinline__ float2 rotate_row(const unsigned char *tile, const float2 *cs, int a) {
     constexpr int N = 128 * MH, NK = N / 16;
     float yr = 0.0f, yi = 0.0f;
-    const unsigned char *row = tile + (a >> 3) * 256 + (a & 7) * 16;
+    const int al = a & 127;
+    const unsigned char *row = tile + (size_t)(a >> 7) * (NK / 2) * kStageBytes + (al >> 3) * 256 + (al & 7) * 16;
 #pragma unroll 8
-    for (int kh = 0; kh < 2 * NK; ++kh) {  // 8 levels b at a time: K-block kh/2, core column kh%2
-        const unsigned char *blk = row + (size_t)(kh >> 1) * N * 64 + (kh & 1) * 128;
+    for (int kh = 0; kh < 2 * NK; ++kh) {  // 8 levels b at a time: K-block kb = kh/2, core column kh%2
+        const int kb = kh >> 1;
+        const unsigned char *blk = row + (size_t)(kb >> 1) * kStageBytes + (kb & 1) * 4096 + (kh & 1) * 128;
         uint4 w[2];
-        w[0] = *reinterpret_cast<const uint4 *>(blk);           // hi
-        w[1] = *reinterpret_cast<const uint4 *>(blk + N * 32);  // lo
+        w[0] = *reinterpret_cast<const uint4 *>(blk);         // hi
+        w[1] = *reinterpret_cast<const uint4 *>(blk + 8192);  // lo
         const __half2 *hh = reinterpret_cast<const __half2 *>(w);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     unsigned char *sB_hi = smem;
     unsigned char *sB_lo = smem + b_bytes;
     unsigned char *sA = smem + 2 * b_bytes;
-    const uint32_t stage_bytes = (uint32_t)N * 64;  // one K-block of 16 levels: FP16 hi then lo, all N rows
+    const uint32_t stage_bytes = kStageBytes;
     unsigned char *misc = sA + (size_t)kStages * stage_bytes;
     TcShared S;
     S.bars = reinterpret_cast<uint64_t *>(misc);  // 2 kStages + 2 barriers (4 reserved)
@@ -316,7 +321,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.red = reinterpret_cast<float *>(S.cst + N);
 
     const uint32_t bar_full = smem_u32(S.bars), bar_empty = bar_full + 8 * kStages;
-    const uint32_t bar_dfull = bar_full + 16 * kStages, bar_bready = bar_dfull + 8;
+    // rowsA / rowsB: the next operand's levels [0, N/2) / [N/2, N) are written and
+    // the products of block h = 0 / h = 1 read
+    const uint32_t bar_dfull = bar_full + 16 * kStages, bar_rowsA = bar_dfull + 8, bar_rowsB = bar_rowsA + 8;
     const int64_t t0 = (int64_t)blockIdx.x * TT;
 
     if (tid == 0) {
@@ -325,7 +332,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             mbar_init(bar_empty + 8 * s, 1);
         }
         mbar_init(bar_dfull, 1);
-        mbar_init(bar_bready, kEpiThreads);
+        mbar_init(bar_rowsA, kEpiThreads);
+        mbar_init(bar_rowsB, kEpiThreads);
         *S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             bool run = true;
             for (int g = 1; g < K && run && !*S.abort_flag; ++g) {
                 warm(g);
-                for (int s = 0; s < NK; ++s, ++it) {
+                for (int s = 0; s < MH * NK / 2; ++s, ++it) {
                     const int slot = (int)(it % kStages);
                     if (it >= kStages && !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1),
                                                     S.abort_flag, p.status, kSiteSlot)) {
@@ -379,51 +387,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        // Per step, once the epilogue has written the operand (bready): K-blocks
-        // 0..NK-1, each feeding both 128-level blocks of the products; dfull tells
-        // the epilogue that all products are done.
+        // Per step: block h = 0 of the products over K-blocks 0..NK-1, then h = 1,
+        // two K-blocks per ring stage. K-blocks below NK/2 read the operand's
+        // levels [0, N/2), written by the epilogue before rowsA; the rest need
+        // rowsB. dfull tells the epilogue that all products are done.
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (0u << 7) | (0u << 10) | (0u << 15) | (1u << 16) |
                                    ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
             const uint32_t a_lbo = 128, a_sbo = 256;
             const uint32_t b_lbo = (uint32_t)NC * 16, b_sbo = 128;
             const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
-            // ring slot 0 (A, hi half, block h = 0) and K-block 0 (B): every other
-            // operand is these plus a byte offset (shared-memory addresses < 256 KB
-            // keep the 14-bit address field from overflowing)
+            // ring slot 0 and K-block 0 of the operand: every other descriptor is
+            // these plus (byte offset >> 4) in the address field (shared-memory
+            // addresses < 256 KB keep the 14-bit field from overflowing)
             const uint64_t dA = umma_desc(smem_u32(sA), a_lbo, a_sbo);
             const uint64_t dBh = umma_desc(bhi, b_lbo, b_sbo), dBl = umma_desc(blo, b_lbo, b_sbo);
-            uint32_t dcol[MH];
-#pragma unroll
-            for (int h = 0; h < MH; ++h) dcol[h] = tmem + (uint32_t)(h * NC);
             long long it = 0;
             uint32_t last_bar = 0, last_par = 0;
             bool run = true;
             for (int g = 1; g < K && run; ++g) {
-                if (!mbar_wait(bar_bready, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteBReady)) break;
-                fence_after();
-                for (int kb = 0; kb < NK; ++kb, ++it) {
-                    const int slot = (int)(it % kStages);
-                    if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status,
-                                   kSiteFull)) {
-                        run = false;
-                        break;
-                    }
-                    fence_after();
-                    // descriptors advance by (byte offset >> 4) in their address field
-                    const uint64_t a0 = dA + ((uint64_t)slot * stage_bytes >> 4);
-                    const uint64_t bk = (uint64_t)kb * NC * 2;  // kb * NC * 32 bytes
+                for (int h = 0; h < MH && run; ++h)
+                    for (int kp = 0; kp < NK / 2; ++kp, ++it) {
+                        if (h == 0 && (kp == 0 || kp == NK / 4)) {
+                            if (!mbar_wait(kp == 0 ? bar_rowsA : bar_rowsB, (uint32_t)((g - 1) & 1), S.abort_flag,
+                                           p.status, kSiteBReady)) {
+                                run = false;
+                                break;
+                            }
+                            fence_after();
+                        }
+                        const int slot = (int)(it % kStages);
+                        if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status,
+                                       kSiteFull)) {
+                            run = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint64_t a0 = dA + ((uint64_t)slot * stage_bytes >> 4);
+                        const uint32_t d = tmem + (uint32_t)(h * NC);
 #pragma unroll
-                    for (int h = 0; h < MH; ++h) {
-                        const uint64_t ahi = a0 + (uint64_t)h * 256, alo = ahi + (uint64_t)N * 2;
-                        umma_f16(dcol[h], ahi, dBh + bk, idesc, kb > 0 ? 1u : 0u);
-                        umma_f16(dcol[h], ahi, dBl + bk, idesc, 1u);
-                        umma_f16(dcol[h], alo, dBh + bk, idesc, 1u);
+                        for (int u = 0; u < 2; ++u) {
+                            const int kb = 2 * kp + u;
+                            const uint64_t ahi = a0 + (uint64_t)u * 256, alo = ahi + 512;  // +4096 B, +8192 B
+                            const uint64_t bk = (uint64_t)kb * NC * 2;                    // kb * NC * 32 B
+                            umma_f16(d, ahi, dBh + bk, idesc, kb > 0 ? 1u : 0u);
+                            umma_f16(d, ahi, dBl + bk, idesc, 1u);
+                            umma_f16(d, alo, dBh + bk, idesc, 1u);
+                        }
+                        umma_commit(bar_empty + 8 * slot);
+                        last_bar = bar_empty + 8 * slot;
+                        last_par = (uint32_t)((it / kStages) & 1);
                     }
-                    umma_commit(bar_empty + 8 * slot);
-                    last_bar = bar_empty + 8 * slot;
-                    last_par = (uint32_t)((it / kStages) & 1);
-                }
                 if (run) umma_commit(bar_dfull);
             }
             // on an abort, let the products already issued finish (bounded)
@@ -549,7 +563,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         fence_before();
-        mbar_arrive(bar_bready);
+        mbar_arrive(bar_rowsA);
+        mbar_arrive(bar_rowsB);
 
         // per-level factors of the next grid point, loaded one step ahead
         float4 Lnext[MH];
@@ -612,79 +627,95 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     fence_after();
                     if (etid == 0) *S.pcount = 0;
                 }
-                // one chunk of 8 columns: the operand rows of this thread's levels and, at
-                // the last grid point (no next rotation), the sums over levels
-                auto process = [&](int c, uint32_t (&r)[MH][8]) {
-                    float ki[4];
+                // last grid point (no next rotation): the sums over levels from D, one pass
+                // over both blocks of levels
+                if (last) {
+                    auto process = [&](int c, uint32_t (&r)[MH][8]) {
+                        float ki[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
-                    if (!last) {
+                        for (int j = 0; j < 4; ++j) ki[j] = S.kinv[4 * c + j];
+                        float v16[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
 #pragma unroll
                         for (int h = 0; h < MH; ++h) {
-                            float v[8];
+                            const int a = 128 * h + 32 * q + lane;
+                            const float w = L[h].z, d2 = L[h].w;
+                            const bool in_gs = a < gs;
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
-                                const float fr = e2r[h] * ki[j], fi = e2i[h] * ki[j];
+                                // |D|^2 kinv^2: the scale the sums have at the other grid points
+                                const float qv = fmaf(re, re, im * im) * ki[j] * ki[j];
+                                v16[j] += qv;
+                                v16[4 + j] = fmaf(qv, w, v16[4 + j]);
+                                if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
+                            }
+                        }
+                        const float tot = reduce_scatter16(v16, lane);
+                        if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+                    };
+                    for (int c = c_begin; c < c_end; ++c) {
+                        uint32_t r[MH][8];
+#pragma unroll
+                        for (int h = 0; h < MH; ++h)
+                            tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r[h]);
+                        tmem_wait();
+#pragma unroll
+                        for (int h = 0; h < MH; ++h) reg_fence(r[h]);
+                        process(c, r);
+                    }
+                } else {
+                    // pass 1, block by block of 128 levels: the operand rows of this thread's
+                    // level; once block 0 is written (and its products read) the next
+                    // rotation may start on the operand's first half of levels
+#pragma unroll
+                    for (int h = 0; h < MH; ++h) {
+                        auto process = [&](int c, uint32_t (&r)[8]) {
+                            float v[8];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float ki = S.kinv[4 * c + j];
+                                const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
+                                const float fr = e2r[h] * ki, fi = e2i[h] * ki;
                                 v[2 * j] = fmaf(re, fr, -im * fi);
                                 v[2 * j + 1] = fmaf(re, fi, im * fr);
                             }
                             store_chunk(sB_hi, sB_lo, NC, 128 * h + 32 * q + lane, c, v);
+                        };
+                        auto issue = [&](int c, uint32_t (&r)[8]) {
+                            tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r);
+                        };
+                        // the loads of chunk c+1 are in flight while chunk c is processed
+                        uint32_t rA[8], rB[8];
+                        int c = c_begin;
+                        if (c < c_end) issue(c, rA);
+                        tmem_wait();
+                        reg_fence(rA);
+                        while (c < c_end) {
+                            if (c + 1 < c_end) issue(c + 1, rB);
+                            process(c, rA);
+                            tmem_wait();
+                            reg_fence(rB);
+                            if (++c >= c_end) break;
+                            if (c + 1 < c_end) issue(c + 1, rA);
+                            process(c, rB);
+                            tmem_wait();
+                            reg_fence(rA);
+                            ++c;
                         }
-                        return;
-                    }
-                    float v16[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
-#pragma unroll
-                    for (int h = 0; h < MH; ++h) {
-                        const int a = 128 * h + 32 * q + lane;
-                        const float w = L[h].z, d2 = L[h].w;
-                        const bool in_gs = a < gs;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float re = __uint_as_float(r[h][2 * j]), im = __uint_as_float(r[h][2 * j + 1]);
-                            // |D|^2 kinv^2: the scale of the operand rows written in the other form
-                            const float qv = fmaf(re, re, im * im) * ki[j] * ki[j];
-                            v16[j] += qv;
-                            v16[4 + j] = fmaf(qv, w, v16[4 + j]);
-                            if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
+                        if (MH == 2 && h == 0) {
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            fence_before();
+                            mbar_arrive(bar_rowsA);
                         }
-                    }
-                    const float tot = reduce_scatter16(v16, lane);
-                    if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
-                };
-                auto issue = [&](int c, uint32_t (&r)[MH][8]) {
-#pragma unroll
-                    for (int h = 0; h < MH; ++h)
-                        tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r[h]);
-                };
-                auto settle = [&](uint32_t (&r)[MH][8]) {
-                    tmem_wait();
-#pragma unroll
-                    for (int h = 0; h < MH; ++h) reg_fence(r[h]);
-                };
-                // the loads of chunk c+1 are in flight while chunk c is processed
-                {
-                    uint32_t rA[MH][8], rB[MH][8];
-                    int c = c_begin;
-                    if (c < c_end) issue(c, rA);
-                    settle(rA);
-                    while (c < c_end) {
-                        if (c + 1 < c_end) issue(c + 1, rB);
-                        process(c, rA);
-                        settle(rB);
-                        if (++c >= c_end) break;
-                        if (c + 1 < c_end) issue(c + 1, rA);
-                        process(c, rB);
-                        settle(rA);
-                        ++c;
                     }
                 }
-                // the operand is written and the products read: the next step may start
+                // the operand is written and the products read: the next step may go on
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 fence_before();
-                mbar_arrive(bar_bready);
+                if (MH == 1 || last) mbar_arrive(bar_rowsA);
+                mbar_arrive(bar_rowsB);
             }
             if (stop) break;
             // ---- sums over levels from the operand just written (B = D E^2 kinv), while the
@@ -894,7 +925,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
 
 size_t tc_smem_bytes(int N, int TT) {
     const int NC = 2 * TT, nchunk = NC / 8;
-    size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * N * 64;
+    size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * kStageBytes;
     b += 8 * (2 * kStages + 4) + 16 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 4) + 16 +
          (size_t)4 * nchunk * 16 * 4 + (size_t)N * 8;
     b = (b + 1023) & ~(size_t)1023;
