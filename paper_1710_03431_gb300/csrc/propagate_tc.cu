@@ -198,7 +198,7 @@ struct TcShared {
     volatile int *abort_flag;
     int *epi_ok;  // the epilogue's go/stop decision for the current wait, one writer
     uint32_t *tmem_base;
-    uint64_t *bars;  // full[kStages], empty[kStages], dfull, rowsA, rowsB
+    uint64_t *bars;  // full[kStages], empty[kStages], dfull, rowsA, rowsB, b1lo
 };
 
 // Epilogue threads write the rows of B (levels a of this thread) for one
@@ -324,6 +324,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     // rowsA / rowsB: the next operand's levels [0, N/2) / [N/2, N) are written and
     // the products of block h = 0 / h = 1 read
     const uint32_t bar_dfull = bar_full + 16 * kStages, bar_rowsA = bar_dfull + 8, bar_rowsB = bar_rowsA + 8;
+    // b1lo: the products of block h = 1 no longer read the operand's first half
+    // of levels (all products of block 0 are done too)
+    const uint32_t bar_b1lo = bar_rowsB + 8;
     const int64_t t0 = (int64_t)blockIdx.x * TT;
 
     if (tid == 0) {
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         mbar_init(bar_dfull, 1);
         mbar_init(bar_rowsA, kEpiThreads);
         mbar_init(bar_rowsB, kEpiThreads);
+        mbar_init(bar_b1lo, 1);
         *S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -437,6 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         umma_commit(bar_empty + 8 * slot);
                         last_bar = bar_empty + 8 * slot;
                         last_par = (uint32_t)((it / kStages) & 1);
+                        if (MH == 2 && h == 1 && kp == NK / 4 - 1) umma_commit(bar_b1lo);
                     }
                 if (run) umma_commit(bar_dfull);
             }
@@ -598,24 +603,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             // operand is released to the next step's products before this step's jump
             // decisions are known; a trajectory that jumps gets its next product from
             // the patch buffer.
+            // Phases: with two blocks of levels, block 0 of the products is complete and
+            // the running rotation has stopped reading the operand's first half at b1lo,
+            // so pass 1 of block 0 overlaps the rest of the rotation; block 1 follows
+            // dfull. One phase at the last grid point and for a single block.
             bool stop = false;
-            {
+            const int nph = (last || MH == 1) ? 1 : MH;
+            for (int ph = 0; ph < nph && !stop; ++ph) {
                 // one thread waits; all epilogue threads then take the same decision
                 // (a bounded wait can expire for one thread only)
                 if (etid == 0)
-                    *S.epi_ok = mbar_wait(bar_dfull, (uint32_t)((g - 1) & 1), S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
+                    *S.epi_ok = mbar_wait(nph == 2 && ph == 0 ? bar_b1lo : bar_dfull, (uint32_t)((g - 1) & 1),
+                                          S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
                 epi_sync();
-                if (!*S.epi_ok) stop = true;
-            }
-            if (!stop) {
+                if (!*S.epi_ok) {
+                    stop = true;
+                    break;
+                }
                 fence_after();
+                const int hlo = nph == 2 ? ph : 0, hhi = nph == 2 ? ph + 1 : MH;
                 // trajectories that jumped last step: their products come from the patch buffer
                 if (*S.pcount > 0) {
                     if (ch == 0) {
                         for (int i = 0; i < *S.pcount; ++i) {
                             const int t = S.plist[i];
-#pragma unroll
-                            for (int h = 0; h < MH; ++h) {
+                            for (int h = hlo; h < hhi; ++h) {
                                 const float2 y = patch[(size_t)t * N + 128 * h + 32 * q + lane];
                                 tmem_st2(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 2 * t), y.x, y.y);
                             }
@@ -625,10 +637,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     fence_before();
                     epi_sync();
                     fence_after();
-                    if (etid == 0) *S.pcount = 0;
+                    if (ph == nph - 1 && etid == 0) *S.pcount = 0;
                 }
-                // last grid point (no next rotation): the sums over levels from D, one pass
-                // over both blocks of levels
                 if (last) {
                     auto process = [&](int c, uint32_t (&r)[MH][8]) {
                         float ki[4];
@@ -666,11 +676,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         process(c, r);
                     }
                 } else {
-                    // pass 1, block by block of 128 levels: the operand rows of this thread's
-                    // level; once block 0 is written (and its products read) the next
-                    // rotation may start on the operand's first half of levels
+                    // pass 1 of this phase's blocks of 128 levels: the operand rows of this
+                    // thread's level
 #pragma unroll
                     for (int h = 0; h < MH; ++h) {
+                        if (h < hlo || h >= hhi) continue;
                         auto process = [&](int c, uint32_t (&r)[8]) {
                             float v[8];
 #pragma unroll
@@ -704,18 +714,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                             reg_fence(rA);
                             ++c;
                         }
-                        if (MH == 2 && h == 0) {
-                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            fence_before();
-                            mbar_arrive(bar_rowsA);
-                        }
                     }
                 }
-                // the operand is written and the products read: the next step may go on
+                // this phase's operand rows are written and its products read
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 fence_before();
-                if (MH == 1 || last) mbar_arrive(bar_rowsA);
-                mbar_arrive(bar_rowsB);
+                if (nph == 1) {
+                    mbar_arrive(bar_rowsA);
+                    mbar_arrive(bar_rowsB);
+                } else {
+                    mbar_arrive(ph == 0 ? bar_rowsA : bar_rowsB);
+                }
             }
             if (stop) break;
             // ---- sums over levels from the operand just written (B = D E^2 kinv), while the
