@@ -4,7 +4,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/aqt.h"
@@ -29,6 +32,31 @@ struct Bath {
 
 bool sym_eigen(int n, double *A, double *evals, double *V);
 
+// Allocator whose value-initialisation leaves trivial elements uninitialised:
+// the large tables are written in full by the (threaded) builder, so zero
+// filling them first only costs time.
+template <typename T, typename A = std::allocator<T>>
+class default_init_allocator : public A {
+    using traits = std::allocator_traits<A>;
+
+   public:
+    template <typename U>
+    struct rebind {
+        using other = default_init_allocator<U, typename traits::template rebind_alloc<U>>;
+    };
+    using A::A;
+    template <typename U>
+    void construct(U *ptr) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new (static_cast<void *>(ptr)) U;
+    }
+    template <typename U, typename... Args>
+    void construct(U *ptr, Args &&...args) {
+        traits::construct(static_cast<A &>(*this), ptr, std::forward<Args>(args)...);
+    }
+};
+template <typename T>
+using hvec = std::vector<T, default_init_allocator<T>>;
+
 // --------------------------------------------------------------- tables -----
 // Per-grid-point metadata (device-visible POD).
 struct GridMeta {
@@ -42,21 +70,21 @@ struct GridMeta {
 struct Tables {
     int n = 0, N = 0, K = 0;
     double dt = 0.0, tau = 0.0;
-    std::vector<double> evals;   // [K][N]
-    std::vector<double> V;       // [K][N][N]  row x, column a
+    hvec<double> evals;          // [K][N]
+    hvec<double> V;              // [K][N][N]  row x, column a
     std::vector<double> kdiag;   // [K][N][2]  diag of the eigenframe H_eff
     std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
     std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
     std::vector<double> G;       // [K][n][N]  sum_a gamma(w_ab) M_alpha[a,b]^2
     // jump amplitudes, source-major: Rt[g][alpha][b][a] = R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b],
     // M_alpha = V^T sz_alpha V; FP64 for the FP64 path, FP32 (Rt32) for the others
-    std::vector<double> Rt;      // [K][n][N][N]
-    std::vector<float> Rt32;     // [K][n][N][N]
+    hvec<double> Rt;             // [K][n][N][N]
+    hvec<float> Rt32;            // [K][n][N][N]
     std::vector<double> lvlE;    // [K][N]     energy of each level's manifold
     std::vector<int32_t> mfirst; // [K][N]     first level of each level's manifold
     std::vector<int32_t> msize;  // [K][N]     size of each level's manifold
     std::vector<GridMeta> meta;  // [K]
-    std::vector<double> OT;      // [K-1][N][N] transpose of O_g = V_{g+1}^T V_g: OT[b][a] = O[a][b]
+    hvec<double> OT;             // [K-1][N][N] transpose of O_g = V_{g+1}^T V_g: OT[b][a] = O[a][b]
 };
 
 struct Inputs {

@@ -383,7 +383,7 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
         // matrices: core (a/8, k/8) at ((a/8)*2 + k/8)*128 bytes, row a%8 at 16
         // bytes, column k%8 at 2 bytes (a, k local to the block).
         const size_t N = t.N, NK = N / 16, K = t.K, MH = N / 128;
-        std::vector<__half> o16((K - 1) * N * N * 2);
+        hvec<__half> o16((K - 1) * N * N * 2);
         parallel_rows(K - 1, [&](size_t g) {
             for (size_t h = 0; h < MH; ++h)
                 for (size_t kb = 0; kb < NK; ++kb) {

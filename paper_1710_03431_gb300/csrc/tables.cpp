@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <thread>
 
@@ -76,6 +77,22 @@ void gram(const double *X, const double *Y, int ni, int nj, int len, double *out
         }
 }
 
+// Ascending sort of non-negative doubles (their bit patterns order like the
+// values): least-significant-digit radix sort, 11-bit digits.
+void sort_nonnegative(std::vector<double> &w) {
+    const size_t n = w.size();
+    std::vector<uint64_t> a(n), b(n);
+    std::memcpy(a.data(), w.data(), n * 8);
+    for (int shift = 0; shift < 64; shift += 11) {
+        std::vector<size_t> cnt(2049, 0);
+        for (size_t i = 0; i < n; ++i) ++cnt[((a[i] >> shift) & 2047) + 1];
+        for (int d = 0; d < 2048; ++d) cnt[d + 1] += cnt[d];
+        for (size_t i = 0; i < n; ++i) b[cnt[(a[i] >> shift) & 2047]++] = a[i];
+        a.swap(b);
+    }
+    std::memcpy(w.data(), a.data(), n * 8);
+}
+
 void schedule_at(const Inputs &in, double s, double *A, double *B) {
     const auto &ks = in.ks;
     size_t j = 0;
@@ -95,20 +112,20 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.dt = in.t_f / (K - 1);
     tab.tau = 0.5 * tab.dt;
     const size_t NN = (size_t)N * N;
-    tab.evals.assign((size_t)K * N, 0.0);
-    tab.V.assign((size_t)K * NN, 0.0);
+    tab.evals.resize((size_t)K * N);  // written in full below
+    tab.V.resize((size_t)K * NN);
     tab.kdiag.assign((size_t)K * N * 2, 0.0);
     tab.ehalf.assign((size_t)K * N * 2, 0.0);
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
     const bool r64 = in.precision == AQT_PREC_FP64;
-    tab.Rt.assign(r64 ? (size_t)K * n * NN : 0, 0.0);
-    tab.Rt32.assign(r64 ? 0 : (size_t)K * n * NN, 0.0f);
+    tab.Rt.resize(r64 ? (size_t)K * n * NN : 0);
+    tab.Rt32.resize(r64 ? 0 : (size_t)K * n * NN);
     tab.lvlE.assign((size_t)K * N, 0.0);
     tab.mfirst.assign((size_t)K * N, 0);
     tab.msize.assign((size_t)K * N, 0);
     tab.meta.assign(K, GridMeta{0, 1, 1, 0, 0.0});
-    tab.OT.assign((size_t)(K - 1) * NN, 0.0);
+    tab.OT.resize((size_t)(K - 1) * NN);
 
     // classical energies sum_i hz_i z_i + sum_{i<j} J_ij z_i z_j, z = 1 - 2 bit
     std::vector<double> Ez(N, 0.0);
@@ -194,15 +211,17 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         }
         // Bohr classes over manifold pairs must be tight chains; a grid point is
         // "simple" when every class of nonzero frequency holds one manifold pair.
+        // The negative frequencies mirror the positive ones, and no chain crosses
+        // zero (distinct manifolds are more than tol apart), so the positive half
+        // decides both.
         meta.simple = 1;
         {
             const size_t nm = E.size();
             std::vector<double> w;
-            w.reserve(nm * (nm - 1));
+            w.reserve(nm * (nm - 1) / 2);
             for (size_t ma = 0; ma < nm; ++ma)
-                for (size_t mb = 0; mb < nm; ++mb)
-                    if (ma != mb) w.push_back(E[mb] - E[ma]);
-            std::sort(w.begin(), w.end());
+                for (size_t mb = ma + 1; mb < nm; ++mb) w.push_back(E[mb] - E[ma]);
+            sort_nonnegative(w);
             size_t st0 = 0;
             for (size_t i = 1; i <= w.size(); ++i) {
                 if (i == w.size() || w[i] - w[i - 1] > tol) {
@@ -292,13 +311,15 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         }
         // jump operators with their rates absorbed (Eq. Aired): R = sqrt(gamma) M,
         // stored source-major (Rt[b][a] = R[a][b]; M is symmetric)
-        for (auto &x : gam) x = std::sqrt(x);
+        std::vector<double> sgT(NN);  // sqrt(gamma(w_ab)) at [b][a]
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) sgT[(size_t)b * N + a] = std::sqrt(gam[(size_t)a * N + b]);
         for (int al = 0; al < n; ++al) {
             const double *Ma = Mg + (size_t)al * NN;
             const size_t base = ((size_t)g * n + al) * NN;
             for (int b = 0; b < N; ++b)
                 for (int a = 0; a < N; ++a) {
-                    const double r = gam[(size_t)a * N + b] * Ma[(size_t)b * N + a];
+                    const double r = sgT[(size_t)b * N + a] * Ma[(size_t)b * N + a];
                     if (r64) tab.Rt[base + (size_t)b * N + a] = r;
                     else tab.Rt32[base + (size_t)b * N + a] = (float)r;
                 }
