@@ -211,6 +211,16 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// The same split from a packed pair, with packed FP32x2 arithmetic (same
+// roundings as split2).
+__device__ __forceinline__ void split2p(float2 x, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __float22half2_rn(x);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __float22half2_rn(__ffma2_rn(hf, make_float2(-1.0f, -1.0f), x));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ void store_chunk(unsigned char *sB_hi, unsigned char *sB_lo, int NC, int a, int c,
                                             const float v[8]) {
     uint4 ph, pl;
@@ -682,16 +692,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     for (int h = 0; h < MH; ++h) {
                         if (h < hlo || h >= hhi) continue;
                         auto process = [&](int c, uint32_t (&r)[8]) {
-                            float v[8];
+                            // v = D E^2 kinv per trajectory in packed FP32x2 arithmetic (the
+                            // same roundings as the scalar form), split into FP16 hi / lo
+                            const float4 k4 = *reinterpret_cast<const float4 *>(S.kinv + 4 * c);
+                            const float kj[4] = {k4.x, k4.y, k4.z, k4.w};
+                            const float2 e2 = make_float2(e2r[h], e2i[h]);
+                            uint32_t ph[4], pl[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                const float ki = S.kinv[4 * c + j];
                                 const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
-                                const float fr = e2r[h] * ki, fi = e2i[h] * ki;
-                                v[2 * j] = fmaf(re, fr, -im * fi);
-                                v[2 * j + 1] = fmaf(re, fi, im * fr);
+                                const float2 f = __fmul2_rn(e2, make_float2(kj[j], kj[j]));  // (fr, fi)
+                                const float2 v = __ffma2_rn(make_float2(re, re), f,
+                                                            __fmul2_rn(make_float2(im, im), make_float2(-f.y, f.x)));
+                                split2p(v, ph[j], pl[j]);
                             }
-                            store_chunk(sB_hi, sB_lo, NC, 128 * h + 32 * q + lane, c, v);
+                            const int a = 128 * h + 32 * q + lane;
+                            const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
+                            *reinterpret_cast<uint4 *>(sB_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                            *reinterpret_cast<uint4 *>(sB_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                         };
                         auto issue = [&](int c, uint32_t (&r)[8]) {
                             tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r);
