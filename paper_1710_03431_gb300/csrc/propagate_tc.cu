@@ -174,6 +174,17 @@ __device__ __forceinline__ void tmem_st2(uint32_t addr, float x, float y) {
                  "r"(__float_as_uint(y))
                  : "memory");
 }
+// Store / load four consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st4(uint32_t addr, const float v[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld4_issue(uint32_t addr, uint32_t r[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -351,8 +362,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         *S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // products (MH * NC columns), then 12 columns of parked partial sums per chunk
+    const uint32_t park = (uint32_t)(MH * NC);
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(MH * NC)) ncols <<= 1;
+    while (ncols < (uint32_t)(MH * NC + 12 * nchunk)) ncols <<= 1;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(S.tmem_base)),
                      "r"(ncols));
@@ -697,7 +710,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                             const float4 k4 = *reinterpret_cast<const float4 *>(S.kinv + 4 * c);
                             const float kj[4] = {k4.x, k4.y, k4.z, k4.w};
                             const float2 e2 = make_float2(e2r[h], e2i[h]);
+                            const float w = L[h].z, d2w = L[h].w * L[h].z;
                             uint32_t ph[4], pl[4];
+                            float ps[12];  // this level's share of sum |D|^2 kinv^2 (1, w, d2 w)
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
@@ -705,7 +720,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                                 const float2 v = __ffma2_rn(make_float2(re, re), f,
                                                             __fmul2_rn(make_float2(im, im), make_float2(-f.y, f.x)));
                                 split2p(v, ph[j], pl[j]);
+                                const float qv = fmaf(re, re, im * im) * (kj[j] * kj[j]);
+                                ps[j] = qv;
+                                ps[4 + j] = qv * w;
+                                ps[8 + j] = qv * d2w;
                             }
+                            // park the partial sums in spare TMEM columns (the block-1 pass adds
+                            // its share to block 0's); the warp reductions run beside the next
+                            // rotation
+                            const uint32_t pa = tmem + ((uint32_t)(32 * q) << 16) + park + 12u * (uint32_t)c;
+                            if (h > 0) {
+                                uint32_t o[12];
+                                tmem_ld4_issue(pa, o);
+                                tmem_ld4_issue(pa + 4, o + 4);
+                                tmem_ld4_issue(pa + 8, o + 8);
+                                tmem_wait();
+#pragma unroll
+                                for (int i = 0; i < 12; ++i) {
+                                    asm volatile("" : "+r"(o[i]));
+                                    ps[i] += __uint_as_float(o[i]);
+                                }
+                            }
+                            tmem_st4(pa, ps);
+                            tmem_st4(pa + 4, ps + 4);
+                            tmem_st4(pa + 8, ps + 8);
                             const int a = 128 * h + 32 * q + lane;
                             const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
                             *reinterpret_cast<uint4 *>(sB_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
@@ -735,6 +773,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     }
                 }
                 // this phase's operand rows are written and its products read
+                if (!last) tmem_st_wait();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 fence_before();
                 if (nph == 1) {
@@ -745,34 +784,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 }
             }
             if (stop) break;
-            // ---- sums over levels from the operand just written (B = D E^2 kinv), while the
-            // next rotation runs: |D|^2 kinv^2 = |B|^2 / |E^2|^2 with |E^2|^2 = d2^2 ----------
+            // ---- warp reductions of the partial sums parked by pass 1, while the next
+            // rotation runs (its products use other TMEM columns) ------------------------
             if (!last) {
                 for (int c = c_begin; c < c_end; ++c) {
+                    uint32_t o[12];
+                    const uint32_t pa = tmem + ((uint32_t)(32 * q) << 16) + park + 12u * (uint32_t)c;
+                    tmem_ld4_issue(pa, o);
+                    tmem_ld4_issue(pa + 4, o + 4);
+                    tmem_ld4_issue(pa + 8, o + 8);
+                    tmem_wait();
                     float v16[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v16[i] = 0.0f;
-#pragma unroll
-                    for (int h = 0; h < MH; ++h) {
-                        const int a = 128 * h + 32 * q + lane;
-                        const float w = L[h].z, d2 = L[h].w, d2w = d2 * w, ie = 1.0f / (d2 * d2);
-                        const bool in_gs = a < gs;
-                        const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
-                        uint4 bw[2];
-                        bw[0] = *reinterpret_cast<const uint4 *>(sB_hi + off);
-                        bw[1] = *reinterpret_cast<const uint4 *>(sB_lo + off);
-                        const __half2 *bh = reinterpret_cast<const __half2 *>(bw);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float2 hi = __half22float2(bh[j]), lo = __half22float2(bh[4 + j]);
-                            const float br = hi.x + lo.x, bi = hi.y + lo.y;
-                            const float qv = fmaf(br, br, bi * bi) * ie;
-                            v16[j] += qv;
-                            v16[4 + j] = fmaf(qv, w, v16[4 + j]);
-                            v16[8 + j] = fmaf(qv, d2w, v16[8 + j]);
-                            if (in_gs) v16[12 + j] = fmaf(qv, d2, v16[12 + j]);
-                        }
+                    for (int i = 0; i < 12; ++i) {
+                        asm volatile("" : "+r"(o[i]));
+                        v16[i] = __uint_as_float(o[i]);
                     }
+#pragma unroll
+                    for (int i = 12; i < 16; ++i) v16[i] = 0.0f;
                     const float tot = reduce_scatter16(v16, lane);
                     if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
                 }
@@ -790,6 +819,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         Db += rr[4 + j];
                         Da += rr[8 + j];
                         X += rr[12 + j];
+                    }
+                    if (!last) {
+                        // ground-manifold weight sum_{a < gs} |D_a|^2 kinv^2 d2_a = sum |B_a|^2 / d2_a,
+                        // from the few operand rows it needs
+                        X = 0.f;
+                        for (int a = 0; a < gs; ++a) {
+                            const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16 + j * 4;
+                            const __half2 bh = *reinterpret_cast<const __half2 *>(sB_hi + off);
+                            const __half2 bl = *reinterpret_cast<const __half2 *>(sB_lo + off);
+                            const float br = __low2float(bh) + __low2float(bl), bi = __high2float(bh) + __high2float(bl);
+                            X += fmaf(br, br, bi * bi) / lvl[(size_t)g * N + a].w;
+                        }
                     }
                     S.P[t] = Pt;
                     const float nB = Pt - Db;
@@ -966,7 +1007,8 @@ int tc_shape(int N, int64_t M, int num_sms) {
     int tt = (int)((M + num_sms - 1) / num_sms);
     tt = (tt + 7) & ~7;
     if (tt < 8) tt = 8;
-    while (tt > 8 && (tc_smem_bytes(N, tt) > 227 * 1024 || 2 * tt * (N / 128) > 512 || 2 * tt > 256)) tt -= 8;
+    // shared memory, and tensor-memory columns: products plus parked sums (12 per 8 columns)
+    while (tt > 8 && (tc_smem_bytes(N, tt) > 227 * 1024 || 2 * tt * (N / 128) + 3 * tt > 512 || 2 * tt > 256)) tt -= 8;
     return tt;
 }
 
