@@ -54,6 +54,21 @@ def workload(args):
     return W.cfg_main(t_f=args.tf, M=args.M, n_grid=args.n_grid)
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Trajectory-stream seed of one rank: every rank runs its own M
+    trajectories (weak scaling), on its own Philox key."""
+    return base + rank
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """The job's timed region ends with its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -206,7 +221,7 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     inst = workload(args)
     prec = {"fp32": A.AQT_PREC_FP32, "fp64": A.AQT_PREC_FP64, "f16split": A.AQT_PREC_F16SPLIT}[args.precision]
-    seed = inst.seed + rank
+    seed = rank_seed(inst.seed, rank)
     sess = A.Session(inst, precision=prec, device=local, seed=seed)
     t0 = time.perf_counter()
     sess.build()
@@ -241,10 +256,7 @@ def run_ours(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     kern_ms = [a.elapsed_time(b) for a, b in per]
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(elapsed_ms, dev)
     ms_per_step = elapsed_ms / args.steps
     N, M, K = 1 << inst.n_qubits, sess.M, inst.n_grid
     traj_steps = M * (K - 1)
