@@ -30,6 +30,11 @@ if ROOT not in sys.path:
 METRIC = "trajectory-steps/s"
 UNIT = "trajectory-steps/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes (read + write) of one propagate_tc launch on the 8-qubit, N=256, M=10^4, 2000-point,
+# t_f=10 ns workload, from one ncu capture of the current kernel (dram__bytes_read.sum 650.05 MB +
+# dram__bytes_write.sum 16.02 MB, 1 pass); reported only for that workload and reset to None
+# whenever the kernel changes.
+TC_TRAFFIC = {(8, 256, 10000, 2000, 10.0): 650.05e6 + 16.02e6}
 
 
 def parse():
@@ -307,7 +312,8 @@ def run_ours(args):
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "propagate_tc",
+                "traffic": TC_TRAFFIC.get((inst.n_qubits, N, M, K, float(inst.t_f))), "kernel": "propagate_tc",
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state); "
                                "the split form issues 3x that on the FP16 tensor pipe",
                 "issued_mma_frac": 3.0 * achieved / peak,
