@@ -31,16 +31,17 @@ METRIC = "trajectory-steps/s"
 UNIT = "trajectory-steps/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes (read + write) of one propagate_tc launch on the 8-qubit, N=256, M=10^4, 2000-point,
-# t_f=10 ns workload, from one ncu capture of the current kernel (dram__bytes_read.sum 650.05 MB +
-# dram__bytes_write.sum 16.02 MB, 1 pass); reported only for that workload and reset to None
+# t_f=10 ns workload, from one ncu capture of the current kernel (dram__bytes_read.sum 650.33 MB +
+# dram__bytes_write.sum 16.56 MB, 1 pass); reported only for that workload and reset to None
 # whenever the kernel changes.
-TC_TRAFFIC = {(8, 256, 10000, 2000, 10.0): 650.05e6 + 16.02e6}
+TC_TRAFFIC = {(8, 256, 10000, 2000, 10.0): 650.33e6 + 16.56e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 60 for f16split, 3 for fp32 / fp64, 5 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16split", choices=["f16split", "fp32", "fp64"])
@@ -105,6 +106,12 @@ class ClockSampler:
             threading.Thread(target=self._read, daemon=True).start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        # the timed region starts only once nvidia-smi is answering (bounded wait)
+        t_end = time.perf_counter() + 5.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -219,6 +226,8 @@ def run_ours(args):
     from paper_1710_03431_gb300 import aqt as A
 
     rank, world, local = dist_env()
+    if args.steps is None:  # a timed region of about a second
+        args.steps = {"f16split": 60, "fp32": 3, "fp64": 3}[args.precision]
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -357,6 +366,8 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
+    if args.steps is None:
+        args.steps = 5
     vals = []
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state beyond imports

@@ -136,6 +136,24 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// The same product, A kept in the tensor core's collector buffer for the next
+// product (fill) or taken from it and then released (lastuse): the next
+// product with the same A does not read A from shared memory again.
+__device__ __forceinline__ void umma_f16_afill(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_f16_alastuse(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                  uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -457,8 +475,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                             const int kb = 2 * kp + u;
                             const uint64_t ahi = a0 + (uint64_t)u * 256, alo = ahi + 512;  // +4096 B, +8192 B
                             const uint64_t bk = (uint64_t)kb * NC * 2;                    // kb * NC * 32 B
-                            umma_f16(d, ahi, dBh + bk, idesc, kb > 0 ? 1u : 0u);
-                            umma_f16(d, ahi, dBl + bk, idesc, 1u);
+                            umma_f16_afill(d, ahi, dBh + bk, idesc, kb > 0 ? 1u : 0u);
+                            umma_f16_alastuse(d, ahi, dBl + bk, idesc, 1u);
                             umma_f16(d, alo, dBh + bk, idesc, 1u);
                         }
                         umma_commit(bar_empty + 8 * slot);
