@@ -164,3 +164,22 @@ def test_device_runs_limited_to_256_levels(aqt_lib):
         A.aqt_workspace_size(c)
     assert e.value.status == A.AQT_EINVAL
     A.aqt_destroy(c)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    """No fallback: without the compiled library every entry point raises."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1710_03431_gb300 import aqt\n"
+        "aqt.LIB_PATH = %r\n"
+        "aqt._lib = None\n"
+        "try:\n"
+        "    aqt.aqt_create(0)\n"
+        "except ImportError as e:\n"
+        "    print('raised', e)\n"
+    ) % (__file__.rsplit("/tests/", 1)[0], str(tmp_path / "libaqt.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "raised" in r.stdout and "missing" in r.stdout
