@@ -13,12 +13,20 @@
 
 namespace aqt {
 
-// A: n x n row-major symmetric (destroyed). evals ascending; V row-major with
-// column a the eigenvector of evals[a]. Returns false if QL does not converge.
+namespace {
+// Two-lane FP64 vector (GCC vector extension: NEON on aarch64, SSE2 on x86-64,
+// no target flags); aligned(8) makes accesses through it unaligned-safe.
+typedef double v2d __attribute__((vector_size(16), aligned(8)));
+}  // namespace
+
+// A: n x n row-major symmetric (destroyed; only its lower triangle is read).
+// evals ascending; V row-major with column a the eigenvector of evals[a].
+// Returns false if QL does not converge.
 bool sym_eigen(int n, double *A, double *evals, double *V) {
     std::vector<double> d(n), e(n, 0.0), v(n), p(n), w(n), beta(n, 0.0);
     // --- Householder tridiagonalisation: A = Q T Q^T --------------------------
-    // Step k zeroes A[k+2:, k]; its reflector v_k is kept in A[k+1:, k].
+    // Step k zeroes A[k+2:, k]; its reflector v_k is kept in A[k+1:, k]. Only
+    // the lower triangle of the trailing block is updated and read.
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         double *col = &v[0];
@@ -37,21 +45,39 @@ bool sym_eigen(int n, double *A, double *evals, double *V) {
         col[0] += sgn * alpha;
         // |v|^2 = 2 alpha (alpha + |x_0|) for v = x + sign(x_0) alpha e_1
         const double b = 2.0 / (2.0 * alpha * (alpha + std::fabs(col[0] - sgn * alpha)));
-        // p = b * S v over the trailing block S = A[k+1:, k+1:]
+        // p = b * S v over the trailing block S = A[k+1:, k+1:], read from its
+        // lower triangle only (S is symmetric; the upper triangle is not kept
+        // up to date): row i gives sum_{j<i} S[i][j] v[j] to p[i] and
+        // S[i][j] v[i] to every p[j], j < i, in one pass over the row
+        for (int i = 0; i < m; ++i) p[i] = 0.0;
         for (int i = 0; i < m; ++i) {
             const double *row = &A[(size_t)(k + 1 + i) * n + (k + 1)];
-            double acc = 0.0;
-            for (int j = 0; j < m; ++j) acc += row[j] * col[j];
-            p[i] = b * acc;
+            const double vi = col[i];
+            const v2d viv = {vi, vi};
+            v2d dacc = {0.0, 0.0};
+            int j = 0;
+            for (; j + 2 <= i; j += 2) {
+                const v2d r = *(const v2d *)(row + j);
+                dacc += r * *(const v2d *)(col + j);
+                *(v2d *)(&p[j]) += r * viv;
+            }
+            double dot = dacc[0] + dacc[1];
+            for (; j < i; ++j) {
+                dot += row[j] * col[j];
+                p[j] += row[j] * vi;
+            }
+            p[i] += row[i] * vi + dot;
         }
+        for (int i = 0; i < m; ++i) p[i] *= b;
         double pv = 0.0;
         for (int i = 0; i < m; ++i) pv += p[i] * col[i];
         const double K = 0.5 * b * pv;
         for (int i = 0; i < m; ++i) w[i] = p[i] - K * col[i];
+        // S -= v w^T + w v^T on the lower triangle
         for (int i = 0; i < m; ++i) {
             double *row = &A[(size_t)(k + 1 + i) * n + (k + 1)];
             const double vi = col[i], wi = w[i];
-            for (int j = 0; j < m; ++j) row[j] -= vi * w[j] + wi * col[j];
+            for (int j = 0; j <= i; ++j) row[j] -= vi * w[j] + wi * col[j];
         }
         e[k] = -sgn * alpha;
         beta[k] = b;

@@ -77,6 +77,92 @@ void gram(const double *X, const double *Y, int ni, int nj, int len, double *out
         }
 }
 
+// Two-lane FP64 vector (GCC vector extension: NEON on aarch64, SSE2 on x86-64,
+// no target flags); aligned(8) makes loads through it unaligned-safe.
+typedef double v2d __attribute__((vector_size(16), aligned(8)));
+
+// M_alpha = V^T sz_alpha V for every qubit alpha, written in full into
+// M[alpha][a][b] (V row-major [x][a], N = 2^n). With P_alpha the projector on
+// basis states whose bit alpha is set, sz_alpha = 1 - 2 P_alpha and
+// M_alpha = I - 2 W_alpha, W_alpha[a][b] = sum over x with bit alpha set of
+// V[x][a] V[x][b]. Split x into high bits u and low bits l (x = u 2^nl + l):
+// the partial Gram matrices of the rows sharing u (resp. l) are formed once,
+// and W_alpha for a high (low) bit is the sum of the partials whose u (l) has
+// that bit, which halves the multiply-adds of forming each W_alpha from its
+// own N/2 rows. Register blocks of 4 (a) x 8 (b); only b >= a is formed, the
+// rest mirrored.
+void sz_frames(const double *V, int n, double *M) {
+    const int N = 1 << n, nl = n / 2, nh = n - nl, NU = 1 << nh, NL = 1 << nl;
+    const size_t NN = (size_t)N * N;
+    std::vector<double> Wt((size_t)n * 32);
+    for (int i0 = 0; i0 < N; i0 += 4)
+        for (int j0 = (i0 / 8) * 8; j0 < N; j0 += 8) {
+            const int ib = std::min(4, N - i0), jb = std::min(8, N - j0);
+            std::fill(Wt.begin(), Wt.end(), 0.0);
+            // one partial over the rows of a group: over u (group l) or over l (group u)
+            auto partial = [&](int grp, bool by_u, double *out) {
+                const int cnt = by_u ? NL : NU;
+                if (ib == 4 && jb == 8) {
+                    v2d acc[4][4];
+                    for (int ii = 0; ii < 4; ++ii)
+                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = v2d{0.0, 0.0};
+                    for (int k = 0; k < cnt; ++k) {
+                        const int x = by_u ? (grp << nl) | k : (k << nl) | grp;
+                        const double *r = V + (size_t)x * N;
+                        const v2d *rb = (const v2d *)(r + j0);
+                        const v2d b0 = rb[0], b1 = rb[1], b2 = rb[2], b3 = rb[3];
+                        for (int ii = 0; ii < 4; ++ii) {
+                            const v2d a = {r[i0 + ii], r[i0 + ii]};
+                            acc[ii][0] += a * b0;
+                            acc[ii][1] += a * b1;
+                            acc[ii][2] += a * b2;
+                            acc[ii][3] += a * b3;
+                        }
+                    }
+                    for (int ii = 0; ii < 4; ++ii)
+                        for (int jj = 0; jj < 4; ++jj) {
+                            out[ii * 8 + 2 * jj] = acc[ii][jj][0];
+                            out[ii * 8 + 2 * jj + 1] = acc[ii][jj][1];
+                        }
+                } else {
+                    for (int ii = 0; ii < ib; ++ii)
+                        for (int jj = 0; jj < jb; ++jj) {
+                            double a = 0.0;
+                            for (int k = 0; k < cnt; ++k) {
+                                const int x = by_u ? (grp << nl) | k : (k << nl) | grp;
+                                a += V[(size_t)x * N + i0 + ii] * V[(size_t)x * N + j0 + jj];
+                            }
+                            out[ii * 8 + jj] = a;
+                        }
+                }
+            };
+            double part[32] = {};
+            for (int u = 0; u < NU; ++u) {  // high bits alpha = nl .. n-1
+                partial(u, true, part);
+                for (int al = nl; al < n; ++al)
+                    if ((u >> (al - nl)) & 1)
+                        for (int e = 0; e < 32; ++e) Wt[(size_t)al * 32 + e] += part[e];
+            }
+            for (int l = 0; l < NL && nl > 0; ++l) {  // low bits alpha = 0 .. nl-1
+                partial(l, false, part);
+                for (int al = 0; al < nl; ++al)
+                    if ((l >> al) & 1)
+                        for (int e = 0; e < 32; ++e) Wt[(size_t)al * 32 + e] += part[e];
+            }
+            for (int al = 0; al < n; ++al) {
+                double *Ma = M + (size_t)al * NN;
+                for (int ii = 0; ii < ib; ++ii)
+                    for (int jj = 0; jj < jb; ++jj) {
+                        const int a = i0 + ii, b = j0 + jj;
+                        if (b < a) continue;
+                        const double v = (a == b ? 1.0 : 0.0) - 2.0 * Wt[(size_t)al * 32 + ii * 8 + jj];
+                        Ma[(size_t)a * N + b] = v;
+                        Ma[(size_t)b * N + a] = v;
+                    }
+            }
+        }
+}
+
 // Ascending sort of non-negative doubles (their bit patterns order like the
 // values): least-significant-digit radix sort, 11-bit digits.
 void sort_nonnegative(std::vector<double> &w) {
@@ -234,31 +320,9 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                 }
             }
         }
-        // VT rows are eigenvectors. sz_alpha = 1 - 2 P_alpha with P_alpha the
-        // projector on basis states whose bit alpha is set, so
-        // M_alpha = V^T sz_alpha V = I - 2 W_alpha^T W_alpha, W_alpha = those rows of V.
-        std::vector<double> VT(NN), W((size_t)N * (N / 2)), Wt((size_t)N * N);
-        for (int x = 0; x < N; ++x)
-            for (int a = 0; a < N; ++a) VT[(size_t)a * N + x] = V[(size_t)x * N + a];
         std::vector<double> Mbuf((size_t)n * NN);
         double *Mg = Mbuf.data();
-        for (int al = 0; al < n; ++al) {
-            for (int a = 0; a < N; ++a) {
-                const double *va = &VT[(size_t)a * N];
-                double *wa = &W[(size_t)a * (N / 2)];
-                int k = 0;
-                for (int x = 0; x < N; ++x)
-                    if ((x >> al) & 1) wa[k++] = va[x];
-            }
-            gram(W.data(), W.data(), N, N, N / 2, Wt.data(), N, true);
-            double *Ma = Mg + (size_t)al * NN;
-            for (int a = 0; a < N; ++a)
-                for (int b = a; b < N; ++b) {
-                    const double v = (a == b ? 1.0 : 0.0) - 2.0 * Wt[(size_t)a * N + b];
-                    Ma[(size_t)a * N + b] = v;
-                    Ma[(size_t)b * N + a] = v;
-                }
-        }
+        sz_frames(V, n, Mg);
         // rates: gamma and S per level pair (a <- b), reused over alpha
         std::vector<double> gam(NN), lam(NN);
         for (int a = 0; a < N; ++a)
