@@ -17,6 +17,48 @@ namespace {
 // Two-lane FP64 vector (GCC vector extension: NEON on aarch64, SSE2 on x86-64,
 // no target flags); aligned(8) makes accesses through it unaligned-safe.
 typedef double v2d __attribute__((vector_size(16), aligned(8)));
+// Apply the Givens rotations of one QL sweep to the rows of ZT (n x n,
+// row-major): rotation r mixes rows i = m-1-r and i+1 of every column x as
+//   (z_{i+1}, z_i) <- (s z_i + c z_{i+1}, c z_i - s z_{i+1}),
+// in the order r = 0, 1, ... Columns are independent, so the whole sequence
+// is applied to one block of columns at a time, the row shared by
+// consecutive rotations carried in registers (16 independent two-lane chains
+// per block of 32 columns).
+template <int NV>
+static inline void sweep_block(double *ZT, int n, int m, int nrot, const double *rc, const double *rs, int x0) {
+    v2d t[NV];
+    for (int u = 0; u < NV; ++u) t[u] = *(const v2d *)(ZT + (size_t)m * n + x0 + 2 * u);
+    for (int r = 0; r < nrot; ++r) {
+        const int i = m - 1 - r;
+        const v2d sv = {rs[r], rs[r]}, cv = {rc[r], rc[r]};
+        const v2d *zi = (const v2d *)(ZT + (size_t)i * n + x0);
+        v2d *zi1 = (v2d *)(ZT + (size_t)(i + 1) * n + x0);
+        for (int u = 0; u < NV; ++u) {
+            const v2d z = zi[u];
+            zi1[u] = sv * z + cv * t[u];
+            t[u] = cv * z - sv * t[u];
+        }
+    }
+    v2d *zl = (v2d *)(ZT + (size_t)(m - nrot) * n + x0);
+    for (int u = 0; u < NV; ++u) zl[u] = t[u];
+}
+
+void apply_sweep(double *ZT, int n, int m, int nrot, const double *rc, const double *rs) {
+    if (nrot == 0) return;
+    int x0 = 0;
+    for (; x0 + 32 <= n; x0 += 32) sweep_block<16>(ZT, n, m, nrot, rc, rs, x0);
+    for (; x0 + 8 <= n; x0 += 8) sweep_block<4>(ZT, n, m, nrot, rc, rs, x0);
+    for (; x0 < n; ++x0) {
+        double t = ZT[(size_t)m * n + x0];
+        for (int r = 0; r < nrot; ++r) {
+            const int i = m - 1 - r;
+            const double z = ZT[(size_t)i * n + x0];
+            ZT[(size_t)(i + 1) * n + x0] = rs[r] * z + rc[r] * t;
+            t = rc[r] * z - rs[r] * t;
+        }
+        ZT[(size_t)(m - nrot) * n + x0] = t;
+    }
+}
 }  // namespace
 
 // A: n x n row-major symmetric (destroyed; only its lower triangle is read).
@@ -118,6 +160,7 @@ bool sym_eigen(int n, double *A, double *evals, double *V) {
     double tnorm = 0.0;
     for (int i = 0; i < n; ++i) tnorm = std::max(tnorm, std::fabs(d[i]) + std::fabs(e[i]) + (i ? std::fabs(e[i - 1]) : 0.0));
     const double small = eps * tnorm;
+    std::vector<double> rc(n), rs(n);
     for (int l = 0; l < n; ++l) {
         int iter = 0;
         for (;;) {
@@ -133,6 +176,7 @@ bool sym_eigen(int n, double *A, double *evals, double *V) {
             g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
             double s = 1.0, c = 1.0, pp = 0.0;
             int i = m - 1;
+            int nrot = 0;  // rotations of this sweep, on rows (m-1-r, m-r), r = 0..nrot-1
             bool underflow = false;
             for (; i >= l; --i) {
                 const double f = s * e[i];
@@ -152,14 +196,11 @@ bool sym_eigen(int n, double *A, double *evals, double *V) {
                 pp = s * r;
                 d[i + 1] = g + pp;
                 g = c * r - bb;
-                double *zi = &ZT[(size_t)i * n];
-                double *zi1 = &ZT[(size_t)(i + 1) * n];
-                for (int x = 0; x < n; ++x) {
-                    const double t = zi1[x];
-                    zi1[x] = s * zi[x] + c * t;
-                    zi[x] = c * zi[x] - s * t;
-                }
+                rs[nrot] = s;
+                rc[nrot] = c;
+                ++nrot;
             }
+            apply_sweep(ZT.data(), n, m, nrot, rc.data(), rs.data());
             if (underflow) continue;
             d[l] -= pp;
             e[l] = g;
