@@ -14,7 +14,11 @@ Readings shared with the CUDA path:
     each frozen piece is propagated with scipy's matrix exponential of
     -i H_eff t, H_eff = V K V^T;
   * the jump time inside a piece is the root of ||exp(-i H_eff t) psi||^2 = r,
-    bracketed and solved by Brent's method; a tie (norm equal to r) jumps;
+    bracketed and solved by Brent's method; a tie (norm equal to r) jumps
+    ("refined" timing). With "grid" timing the jump is applied at the end of
+    the piece in which the squared norm fell to r, with the state propagated
+    through the whole piece (the paper's condition checked at time-step
+    resolution only);
   * jump choice with two uniforms (u1, u2). Units (alpha, m, a): qubit alpha,
     source manifold m, target level a, with weight
         w = gamma(E(m) - E(m(a))) |sum_{b in m} M_alpha[a,b] c_b|^2 ,  c = V^T psi .
@@ -96,7 +100,7 @@ class Trajectory:
         self.n_jumps = 0
         self.jumps = []
 
-    def advance(self, piece: Piece, tau: float, t0: float, grid_index: int, half: int):
+    def advance(self, piece: Piece, tau: float, t0: float, grid_index: int, half: int, timing: str = "refined"):
         """Propagate through one frozen piece of length tau starting at t0."""
         psi = self.psi
         elapsed = 0.0
@@ -107,13 +111,17 @@ class Trajectory:
             if np.vdot(trial, trial).real > self.r:
                 self.psi = trial
                 return
+            if timing == "grid":
+                tstar = remaining
+            else:
+                start = psi
+                f = lambda t: np.vdot(v := piece.U(t) @ start, v).real - self.r  # noqa: E731
+                if f(remaining) > 0.0:   # rounding between the two evaluations
+                    self.psi = trial
+                    return
+                tstar = optimize.brentq(f, 0.0, remaining, xtol=1e-16 * max(tau, 1e-30), rtol=1e-15,
+                                        maxiter=200)
             start = psi
-            f = lambda t: np.vdot(v := piece.U(t) @ start, v).real - self.r  # noqa: E731
-            if f(remaining) > 0.0:   # rounding between the two evaluations
-                self.psi = trial
-                return
-            tstar = optimize.brentq(f, 0.0, remaining, xtol=1e-16 * max(tau, 1e-30), rtol=1e-15,
-                                    maxiter=200)
             psi = piece.U(tstar) @ start
             psi = psi / np.linalg.norm(psi)
             self.n_jumps += 1
@@ -133,8 +141,9 @@ class Trajectory:
                 return
 
 
-def sample(inst, traj_ids, seed=None):
-    """Run the given trajectories over the whole grid.
+def sample(inst, traj_ids, seed=None, timing: str = "refined"):
+    """Run the given trajectories over the whole grid (``timing``: "refined" or
+    "grid", see the module docstring).
 
     Returns (p_gs [len(traj_ids), K], jumps (list of dicts), final psi
     [len(traj_ids), N] in the computational basis, normalised).
@@ -154,8 +163,8 @@ def sample(inst, traj_ids, seed=None):
         else:
             t_prev = (k - 1) * dt
             for tr in trajs:
-                tr.advance(prev, tau, t_prev, k - 1, 1)
-                tr.advance(piece, tau, t_prev + tau, k, 0)
+                tr.advance(prev, tau, t_prev, k - 1, 1, timing)
+                tr.advance(piece, tau, t_prev + tau, k, 0, timing)
         g0 = fr.eig.manifolds[0]
         for i, tr in enumerate(trajs):
             c = fr.eig.V[:, g0].T @ tr.psi

@@ -365,3 +365,144 @@ def test_trajectory_average_matches_density_matrix():
         mean = p[:, k].mean()
         se = p[:, k].std(ddof=1) / math.sqrt(M)
         assert abs(mean - ref[k]) < 3.5 * se + 1e-12, (k, mean, ref[k], se)
+
+
+# --- Bohr-frequency classes (Sec. II, Eq. Lindblad2) ----------------------------------------
+# At s = 0 of the linear schedule H_S = -A sum sx with A = 2 pi: the manifolds are
+# k = 0..n (k spins anti-aligned with the field), energy -A (n - 2k), multiplicity
+# C(n, k), so the Bohr frequency of (m_a, m_b) is 2 A (k_b - k_a). The classes
+# below are written out by hand from that arithmetic: (m_a, m_b) pairs, classes
+# in increasing frequency, zero-frequency class first.
+S0_CLASSES = {
+    2: [(0, [(0, 0), (1, 1), (2, 2)]),
+        (-2, [(2, 0)]),
+        (-1, [(1, 0), (2, 1)]),
+        (1, [(0, 1), (1, 2)]),
+        (2, [(0, 2)])],
+    3: [(0, [(0, 0), (1, 1), (2, 2), (3, 3)]),
+        (-3, [(3, 0)]),
+        (-2, [(2, 0), (3, 1)]),
+        (-1, [(1, 0), (2, 1), (3, 2)]),
+        (1, [(0, 1), (1, 2), (2, 3)]),
+        (2, [(0, 2), (1, 3)]),
+        (3, [(0, 3)])],
+}
+
+
+def _classes_as_sets(classes, unit):
+    return [(round(w / unit), sorted(map(tuple, pairs))) for w, pairs in classes]
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_bohr_classes_at_s0_written_out(n):
+    inst = W.tfim_instance(n, 40 + n)
+    eig = model.eigen_at(inst, 0.0)
+    A = 2 * math.pi
+    got = model.bohr_classes(eig)
+    for w, _ in got:
+        assert abs(w / (2 * A) - round(w / (2 * A))) < 1e-12
+    assert _classes_as_sets(got, 2 * A) == [(w, sorted(p)) for w, p in S0_CLASSES[n]]
+
+
+def test_bohr_classes_merge_distinct_pairs_of_equal_frequency():
+    # s = 1 with hz = (1, 1/2), J = 0: levels -3/2, -1/2, 1/2, 3/2 (x 2 pi), all
+    # nondegenerate and equally spaced, so distinct level pairs share each Bohr
+    # frequency: omega = 2 pi has three pairs, 4 pi two, 6 pi one.
+    inst = W.tfim_instance(2, 1)
+    inst.hz = np.array([1.0, 0.5])
+    inst.J = np.zeros((2, 2))
+    eig = model.eigen_at(inst, 1.0)
+    assert eig.nondegenerate
+    got = _classes_as_sets(model.bohr_classes(eig), 2 * math.pi)
+    assert got == [(0, [(0, 0), (1, 1), (2, 2), (3, 3)]),
+                   (-3, [(3, 0)]),
+                   (-2, [(2, 0), (3, 1)]),
+                   (-1, [(1, 0), (2, 1), (3, 2)]),
+                   (1, [(0, 1), (1, 2), (2, 3)]),
+                   (2, [(0, 2), (1, 3)]),
+                   (3, [(0, 3)])]
+
+
+def _fourier_component(H, A, w, T=1e9):
+    """(1/T) int_0^T e^{i w t} e^{iHt} A e^{-iHt} dt in closed form from the
+    eigendecomposition of H (each matrix element oscillates at a difference of
+    two eigenvalues): no tolerance-based grouping of frequencies is involved."""
+    e, U = np.linalg.eigh(H)
+    Ae = U.T @ A @ U
+    d = w + e[:, None] - e[None, :]           # frequency of <a| ... |b> times e^{i w t}
+    avg = np.where(np.abs(d) * T < 1e-3, 1.0 + 0j,
+                   (np.exp(1j * np.clip(d * T, -1e300, 1e300)) - 1) / (1j * np.where(d == 0, 1, d) * T))
+    return U @ (Ae * avg) @ U.T
+
+
+@pytest.mark.parametrize("case", ["s0_n3", "equal_spacing", "generic"])
+def test_class_operators_are_fourier_components(case):
+    """Eq. Lindblad2: L_{alpha,omega} = sum over the class of P_a sz_alpha P_b is
+    the omega-Fourier component of e^{iHt} sz_alpha e^{-iHt}. Checked against
+    the time average computed independently, with sum_omega L = sz_alpha and
+    [H, L] = -omega L. A class split in two, or two frequencies merged, fails."""
+    if case == "s0_n3":
+        inst, s = W.tfim_instance(3, 41), 0.0
+    elif case == "equal_spacing":
+        inst, s = W.tfim_instance(2, 1), 1.0
+        inst.hz, inst.J = np.array([1.0, 0.5]), np.zeros((2, 2))
+    else:
+        inst, s = W.tfim_instance(3, 42), 0.4
+    n = inst.n_qubits
+    HX, HZ = model.hamiltonian_terms(inst)
+    Aa, Bb = model.schedule(inst, s)
+    H = Aa * HX + Bb * HZ
+    eig = model.eigen_at(inst, s)
+    P = [eig.V[:, m] @ eig.V[:, m].T for m in eig.manifolds]
+    classes = model.bohr_classes(eig)
+    ws = [w for w, _ in classes]
+    assert all(abs(a - b) > 1e-6 for i, a in enumerate(ws) for b in ws[i + 1:])   # one class per frequency
+    for al in range(n):
+        Z = model.op_on(al, model.SZ, n)
+        total = np.zeros_like(Z)
+        for w, pairs in classes:
+            L = sum(P[ma] @ Z @ P[mb] for ma, mb in pairs)
+            total = total + L
+            assert np.max(np.abs(H @ L - L @ H + w * L)) < 1e-10
+            assert np.max(np.abs(_fourier_component(H, Z, w) - L)) < 1e-8
+        assert np.max(np.abs(total - Z)) < 1e-12
+
+
+def test_continuous_ame_converges_to_split_at_second_order():
+    """The split-exact AME on the grid converges to the AME integrated without
+    a grid (generator rebuilt at every integrator stage) at O(dt^2), bath on."""
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=5.0, n_grid=21, seed=99)
+    cont = ame.run_continuous(inst)["p_gs"]
+    errs = []
+    for K in (21, 41, 81):
+        inst.n_grid = K
+        split = ame.run(inst)["p_gs"][:: (K - 1) // 20]
+        errs.append(np.max(np.abs(split - cont)))
+    assert errs[0] > 1e-4
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4
+
+
+def test_grid_timing_jumps_at_the_end_of_the_refined_piece():
+    """GRID timing (the norm condition of Sec. IV checked at time-step
+    resolution): with the same random streams, the first jump of a trajectory
+    comes at the end of the frozen piece that holds its refined jump time, with
+    the same qubit (the state before it is the same)."""
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=5.0, n_grid=101, seed=99)
+    M = 60
+    _, jr, _ = trajectories.sample(inst, range(M))
+    _, jg, _ = trajectories.sample(inst, range(M), timing="grid")
+    tau = 0.5 * inst.t_f / (inst.n_grid - 1)
+    fr = {}
+    for j in jr:
+        fr.setdefault(j["traj"], j)
+    fg = {}
+    for j in jg:
+        fg.setdefault(j["traj"], j)
+    assert set(fr) == set(fg) and len(fr) > 20
+    for t, a in fr.items():
+        b = fg[t]
+        assert (a["grid"], a["half"]) == (b["grid"], b["half"])
+        end = (math.floor(a["t"] / tau + 1e-9) + 1) * tau
+        assert abs(b["t"] - end) < 1e-12
+    for j in jg:   # every GRID jump sits on a piece boundary
+        assert abs(j["t"] / tau - round(j["t"] / tau)) < 1e-9
