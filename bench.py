@@ -291,20 +291,16 @@ def run_ours(args):
             A.aqt_set_schedule(ctx2, inst.sched_s, inst.sched_A, inst.sched_B)
             A.aqt_set_bath(ctx2, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
             A.aqt_set_grid(ctx2, inst.t_f, inst.n_grid)
-            A.aqt_set_trajectories(ctx2, M, seed, prec, sess.jcap)
+            A.aqt_set_trajectories(ctx2, M, seed, prec, A.AQT_JUMP_REFINED, sess.jcap)
             A.aqt_bind_workspace(ctx2, ws.data_ptr(), ws.numel())
             A.aqt_build_tables(ctx2, stream.cuda_stream)
             A.aqt_run(ctx2, stream.cuda_stream)
             A.aqt_sync(ctx2)
             m2, s2 = A.aqt_get_observables(ctx2, K)
         e2e_s = (time.perf_counter() - t1) / args.e2e_steps
+        # bytes aqt_build_tables copied to the device (as the library counts them)
+        h2d = int(A.aqt_debug_table(ctx2, 8, 0, (2,))[1])
         A.aqt_destroy(ctx2)
-        rs = 8 if prec == A.AQT_PREC_FP64 else 4
-        tcl = K * N * 16 if prec == A.AQT_PREC_F16SPLIT else 0
-        n = inst.n_qubits
-        # the tables aqt_build_tables copies (jump amplitudes and rotations in the state precision)
-        h2d = (K * N * (2 * 8 + 2 * 8 + 2 * 4 + 8 + 8 + 4 + 4) + K * n * N * 8 + K * n * N * N * rs + K * 24
-               + (K - 1) * N * N * rs + tcl)
         e2e = {"value": world * traj_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(K * 2 * 8 + 12), "seconds_per_step": e2e_s,
                "includes": "set_* + FP64 host table build + H2D + run + sync + observables D2H"}

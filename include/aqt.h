@@ -53,15 +53,21 @@ typedef enum {
     AQT_ENOCONV = 6,    /* eigensolver did not converge */
     AQT_EDEGEN = 7,     /* degenerate structure outside what the GPU path supports */
     AQT_ENODEV = 8,     /* context has no device (created with device -1) */
-    AQT_ETIMEOUT = 9    /* a bounded wait inside the tensor-core kernel expired (about 2 s);
+    AQT_ETIMEOUT = 9,   /* a bounded wait inside the tensor-core kernel expired (about 2 s);
                            the kernel stopped early and freed its resources; outputs are invalid */
+    AQT_WDT = 10        /* warning from aqt_build_tables: the tables are built and usable, but the
+                           grid step is not well below (dt > 0.1 x) a term of the time-step
+                           condition of Sec. IV, Eq. newcond, that applies to the jump timing
+                           (aqt_get_dt_bounds gives the terms) */
 } aqt_status;
 
-/* Propagation precision. The host tables and the jump clock are always FP64;
- * the jump-time root, channel draw and jump operator run in the state's
- * precision (FP64 for AQT_PREC_FP64, FP32 otherwise, with the norm decay kept
- * as expm1 terms so that its relative accuracy does not depend on its size);
- * the jump amplitude table is held in that precision on the device. */
+/* Propagation precision. The host tables, the jump clock, the crossing time
+ * (root of the norm condition of Sec. IV, Newton's method on the FP64 decay
+ * sums formed from the state's populations) and the cumulative sums of both
+ * channel draws (App. B.1, Eq. Pi(t)) are FP64 on every path; the state, its
+ * no-jump propagation and the jump operator's application run in the state's
+ * precision. The eigenvectors, from which a jump forms the column of
+ * V^T sz_alpha V it needs, are held on the device in the state precision. */
 typedef enum {
     AQT_PREC_FP64 = 0,      /* SIMT FP64 state and rotation */
     AQT_PREC_FP32 = 1,      /* SIMT FP32 state and rotation, FP64 norm sums */
@@ -69,6 +75,15 @@ typedef enum {
                                in FP16 with FP32 accumulation (22-bit mantissa), FP32 state;
                                N = 128 or 256 (n_qubits 7 or 8) */
 } aqt_precision;
+
+/* When a jump happens inside a frozen half-step (Sec. IV: the norm of the
+ * unnormalised state falls to the threshold r at t + tau). The paper gives the
+ * condition, not how finely tau is resolved. */
+typedef enum {
+    AQT_JUMP_REFINED = 0,   /* at the root of |psi(t)|^2 = r inside the half-step (FP64 Newton) */
+    AQT_JUMP_GRID = 1       /* at the end of the half-step in which |psi|^2 fell to r: the
+                               time-step-resolution variant, with an O(dt) bias in the jump times */
+} aqt_jump_timing;
 
 /* One jump. t is the jump time in ns; the jump happened while the generator
  * was frozen at grid point `grid`, in the half-step before s_grid (half = 0)
@@ -113,14 +128,19 @@ aqt_status aqt_set_grid(aqt_ctx *ctx, double t_f, int n_grid);
 /* M trajectories, all starting in the ground state of H_S(0) (Sec. V.A).
  * Random streams: Philox4x64-10, key (seed, 0x171003431), counter
  * (trajectory, event, 0, 0); event 0 gives the first threshold, event j the
- * draws of the j-th jump. jump_capacity = records kept on the device. */
-aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int precision,
+ * draws of the j-th jump. jump_timing: aqt_jump_timing. jump_capacity =
+ * records kept on the device. */
+aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int precision, int jump_timing,
                                 int64_t jump_capacity);
 
 /* Device bytes the caller must provide for the current inputs. Device runs
  * take n_qubits <= 8 (N <= 256: the jump warp keeps N/32 levels per lane in
  * registers) and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise AQT_EINVAL
- * (host-only contexts build tables up to n_qubits = 10). */
+ * (host-only contexts build tables up to n_qubits = 10). The size depends on
+ * the spectrum (full jump amplitudes are kept for the grid points with
+ * degenerate levels or coinciding Bohr frequencies), so this call builds the
+ * host tables of aqt_build_tables if they are not built yet, and can return
+ * its errors (AQT_ENOCONV, AQT_EDEGEN). */
 aqt_status aqt_workspace_size(aqt_ctx *ctx, size_t *bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, at least
@@ -131,15 +151,39 @@ aqt_status aqt_bind_workspace(aqt_ctx *ctx, void *dptr, size_t bytes);
 /* Build the FP64 per-grid-point tables (instantaneous eigensystems,
  * degenerate manifolds and Bohr classes per Eq. Lindblad2, the eigenframe
  * H_eff of Eq. Heff, rate tables, frame rotations) on the host, then copy
- * them into the workspace on `stream`. Blocks until the copies are queued and
- * the host buffers may be reused. Errors: AQT_ENOCONV, AQT_EDEGEN, AQT_ECUDA.
- * On a host-only context the tables are built and kept for aqt_debug_table. */
+ * them into the workspace on `stream`. Blocks until the copies are done and
+ * the host buffers may be reused. Errors: AQT_ENOCONV, AQT_EDEGEN, AQT_ECUDA;
+ * warning (tables built and usable): AQT_WDT. On a host-only context the
+ * tables are built and kept for aqt_debug_table. */
 aqt_status aqt_build_tables(aqt_ctx *ctx, void *stream);
+
+/* The three terms of the time-step condition of Sec. IV, Eq. newcond,
+ *   dt << min_t { 2 |H_eff| / |dH_eff/dt|,  1 / |H_eff|,  |lambda / (lambda^2 - dlambda/dt)| },
+ * each minimised over the grid: bounds[3] in ns, at[3] the grid points (at may
+ * be NULL). |.| is the operator norm: |H_eff| = max |K_bb| exactly;
+ * |dH_eff/dt| is an upper estimate (schedule derivative of H_S by the
+ * triangle inequality plus the rate of change of the dissipative and
+ * Lamb-shift diagonal), so the first term is a lower estimate; lambda is taken
+ * per instantaneous eigenstate (lambda_b = -2 Im K_bb, levels whose jump
+ * probability over the run exceeds 1e-6). aqt_build_tables returns AQT_WDT
+ * when dt > 0.1 x the first term, or, with AQT_JUMP_GRID, the third; the
+ * second bounds a first-order no-jump step and does not apply to the exact
+ * frozen-generator phases used here. Needs the host tables (aqt_build_tables
+ * or aqt_workspace_size). */
+aqt_status aqt_get_dt_bounds(aqt_ctx *ctx, double *bounds, int32_t *at);
 
 /* Propagate all trajectories over the whole grid (Sec. IV). Asynchronous on
  * `stream`; results are valid after aqt_sync. Each call restarts from the
  * initial state with the same random streams. */
 aqt_status aqt_run(aqt_ctx *ctx, void *stream);
+
+/* Failure injection for tests (the default needs no call): the poll limit of
+ * the tensor-core kernel's bounded waits between its roles, 0 .. 2^22
+ * (default 2^22; the waits also end after about 2 s). With 0 every such wait
+ * expires at once: the kernel records AQT_ETIMEOUT with the waits' names,
+ * issues no products, waits (with the default limits) for the copies it has
+ * in flight, frees its tensor memory and ends; the context stays usable. */
+aqt_status aqt_set_wait_limit(aqt_ctx *ctx, int64_t polls);
 
 /* Wait for the last run and return its device status: AQT_OK, AQT_EOVERFLOW
  * (jump records dropped), AQT_ENUMERIC or AQT_ETIMEOUT. */
@@ -151,6 +195,13 @@ aqt_status aqt_get_observables(aqt_ctx *ctx, double *mean, double *stderr_);
 
 /* Raw FP64 sums over trajectories, sum_x[n_grid] and sum_x2[n_grid]. */
 aqt_status aqt_get_observable_sums(aqt_ctx *ctx, double *sum_x, double *sum_x2);
+
+/* Precision check of the frame rotation (its own arithmetic, as run): the
+ * largest |(squared norm after a rotation c <- O c) / (before) - 1| over all
+ * trajectories and grid steps of the last run. O is orthogonal, so this is
+ * the rounding of the rotation (split products and FP32 sums on the
+ * tensor-core path); the state is renormalised after every step. */
+aqt_status aqt_get_rotation_error(aqt_ctx *ctx, double *max_rel);
 
 /* Copy up to cap jump records, sorted by (traj, t), to host_buf.
  * *n_out = records copied, *n_dropped = records lost to a full device log. */
@@ -177,8 +228,11 @@ aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
  * held on every GPU that loads the library until the process exits. No
  * device memory is allocated by this call.
  *  - The first call on each device looks up that array's device address
- *    (cudaGetSymbolAddress with the device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress with the device current) and keeps it for that
+ *    device's current context; a new context on the device (after
+ *    cudaDeviceReset) is detected and the address looked up again. Make the
+ *    first call on a device (and the first after a reset) before any stream
+ *    capture.
  *  - A run that needs more than 32 MiB of scratch (it grows with
  *    M x n_grid and with M x N) returns AQT_EINVAL with the size in the message.
  *  - All calls on one device share the array and it keeps the last call's
@@ -192,12 +246,14 @@ aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, 
 
 /* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes
- * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N] (held in
- * FP32 unless the precision is AQT_PREC_FP64); 4 frame rotation
+ * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N] (FP64,
+ * formed from the eigenvectors on request); 4 frame rotation
  * O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1); 5 eigenvectors V [N][N]
  * (column a = level a); 6 manifold energy per level [N]; 7 grid metadata [4]:
  * (some manifold degenerate, ground-manifold size, every Bohr class of
- * nonzero frequency is a single manifold pair, energy tolerance). */
+ * nonzero frequency is a single manifold pair, energy tolerance); 8 [2]:
+ * (number of grid points that keep full jump amplitudes, bytes copied to the
+ * device by the last aqt_build_tables; grid is ignored). */
 aqt_status aqt_debug_table(aqt_ctx *ctx, int which, int grid, double *out);
 
 #ifdef __cplusplus

@@ -14,15 +14,18 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaqt.so")
 
-AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV, AQT_ETIMEOUT = range(10)
+AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV, AQT_ETIMEOUT, \
+    AQT_WDT = range(11)
 AQT_PREC_FP64, AQT_PREC_FP32, AQT_PREC_F16SPLIT = 0, 1, 2
+AQT_JUMP_REFINED, AQT_JUMP_GRID = 0, 1
 STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4: "AQT_EOVERFLOW",
-                5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV", 9: "AQT_ETIMEOUT"}
+                5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV", 9: "AQT_ETIMEOUT",
+                10: "AQT_WDT"}
 
 EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
            "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
-           "aqt_bind_workspace", "aqt_build_tables", "aqt_run", "aqt_sync", "aqt_get_observables",
-           "aqt_get_observable_sums", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
+           "aqt_bind_workspace", "aqt_build_tables", "aqt_get_dt_bounds", "aqt_set_wait_limit", "aqt_run", "aqt_sync", "aqt_get_observables",
+           "aqt_get_observable_sums", "aqt_get_rotation_error", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
            "aqt_run_static_scratch"]
 
 
@@ -60,14 +63,17 @@ def lib():
             "aqt_set_schedule": (I, [P, I, D, D, D]),
             "aqt_set_bath": (I, [P, C.c_double, C.c_double, C.c_double, I]),
             "aqt_set_grid": (I, [P, C.c_double, I]),
-            "aqt_set_trajectories": (I, [P, I64, U64, I, I64]),
+            "aqt_set_trajectories": (I, [P, I64, U64, I, I, I64]),
             "aqt_workspace_size": (I, [P, C.POINTER(SZ)]),
             "aqt_bind_workspace": (I, [P, P, SZ]),
             "aqt_build_tables": (I, [P, P]),
+            "aqt_get_dt_bounds": (I, [P, D, C.POINTER(C.c_int32)]),
+            "aqt_set_wait_limit": (I, [P, I64]),
             "aqt_run": (I, [P, P]),
             "aqt_sync": (I, [P]),
             "aqt_get_observables": (I, [P, D, D]),
             "aqt_get_observable_sums": (I, [P, D, D]),
+            "aqt_get_rotation_error": (I, [P, D]),
             "aqt_get_jumps": (I, [P, C.POINTER(aqt_jump), I64, C.POINTER(I64), C.POINTER(I64)]),
             "aqt_get_final_state": (I, [P, I, D]),
             "aqt_debug_table": (I, [P, I, I, D]),
@@ -130,9 +136,9 @@ def aqt_set_grid(ctx, t_f, n_grid):
     _check(ctx, lib().aqt_set_grid(ctx, float(t_f), int(n_grid)))
 
 
-def aqt_set_trajectories(ctx, M, seed, precision, jump_capacity):
+def aqt_set_trajectories(ctx, M, seed, precision, jump_timing, jump_capacity):
     _check(ctx, lib().aqt_set_trajectories(ctx, int(M), int(seed) & (2**64 - 1), int(precision),
-                                           int(jump_capacity)))
+                                           int(jump_timing), int(jump_capacity)))
 
 
 def aqt_workspace_size(ctx) -> int:
@@ -145,8 +151,24 @@ def aqt_bind_workspace(ctx, dptr: int, nbytes: int):
     _check(ctx, lib().aqt_bind_workspace(ctx, C.c_void_p(dptr), nbytes))
 
 
-def aqt_build_tables(ctx, stream: int = 0):
-    _check(ctx, lib().aqt_build_tables(ctx, C.c_void_p(stream)))
+def aqt_build_tables(ctx, stream: int = 0) -> int:
+    """Returns AQT_OK, or the warning AQT_WDT (tables built and usable); raises on errors."""
+    st = lib().aqt_build_tables(ctx, C.c_void_p(stream))
+    if st not in (AQT_OK, AQT_WDT):
+        _check(ctx, st)
+    return st
+
+
+def aqt_get_dt_bounds(ctx):
+    """The three terms of Eq. newcond minimised over the grid (ns) and their grid points."""
+    b = np.empty(3)
+    at = (C.c_int32 * 3)()
+    _check(ctx, lib().aqt_get_dt_bounds(ctx, _dp(b), at))
+    return b, [int(x) for x in at]
+
+
+def aqt_set_wait_limit(ctx, polls: int):
+    _check(ctx, lib().aqt_set_wait_limit(ctx, int(polls)))
 
 
 def aqt_run(ctx, stream: int = 0):
@@ -171,6 +193,12 @@ def aqt_get_observable_sums(ctx, n_grid: int):
     s1, s2 = np.empty(n_grid), np.empty(n_grid)
     _check(ctx, lib().aqt_get_observable_sums(ctx, _dp(s1), _dp(s2)))
     return s1, s2
+
+
+def aqt_get_rotation_error(ctx) -> float:
+    v = C.c_double()
+    _check(ctx, lib().aqt_get_rotation_error(ctx, C.byref(v)))
+    return v.value
 
 
 def aqt_get_jumps(ctx, cap: int):
@@ -207,7 +235,8 @@ class Session:
     """One context configured from an instance (see ``workloads.Instance``),
     with its workspace held as a torch uint8 tensor on the context's device."""
 
-    def __init__(self, inst, precision=AQT_PREC_FP64, jump_capacity=None, device=0, M=None, seed=None):
+    def __init__(self, inst, precision=AQT_PREC_FP64, jump_capacity=None, device=0, M=None, seed=None,
+                 timing=AQT_JUMP_REFINED):
         self.inst = inst
         self.device = device
         self.M = int(inst.M if M is None else M)
@@ -215,16 +244,16 @@ class Session:
         self.K = inst.n_grid
         self.ctx = aqt_create(device)
         self.jcap = int(jump_capacity if jump_capacity is not None else max(1024, 64 * self.M))
-        self.configure(inst, precision, seed)
+        self.configure(inst, precision, seed, timing)
         self.ws = None
 
-    def configure(self, inst, precision, seed=None):
+    def configure(self, inst, precision, seed=None, timing=AQT_JUMP_REFINED):
         c = self.ctx
         aqt_set_ising(c, inst.n_qubits, inst.hz, inst.J)
         aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
         aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
         aqt_set_grid(c, inst.t_f, inst.n_grid)
-        aqt_set_trajectories(c, self.M, inst.seed if seed is None else seed, precision, self.jcap)
+        aqt_set_trajectories(c, self.M, inst.seed if seed is None else seed, precision, timing, self.jcap)
 
     def allocate(self):
         import torch
@@ -240,7 +269,7 @@ class Session:
 
     def build(self):
         self.allocate()
-        aqt_build_tables(self.ctx, self.stream())
+        return aqt_build_tables(self.ctx, self.stream())
 
     def run(self):
         aqt_run(self.ctx, self.stream())

@@ -76,15 +76,25 @@ struct Tables {
     std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
     std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
     std::vector<double> G;       // [K][n][N]  sum_a gamma(w_ab) M_alpha[a,b]^2
-    // jump amplitudes, source-major: Rt[g][alpha][b][a] = R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b],
-    // M_alpha = V^T sz_alpha V; FP64 for the FP64 path, FP32 (Rt32) for the others
-    hvec<double> Rt;             // [K][n][N][N]
-    hvec<float> Rt32;            // [K][n][N][N]
+    std::vector<double> Mdiag;   // [K][n][N]  M_alpha[b,b], M_alpha = V^T sz_alpha V
+    // Jump amplitudes R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b], kept only
+    // for the grid points that need the general jump routine (a degenerate
+    // manifold, or a Bohr class of nonzero frequency with several level
+    // pairs); source-major: Rgen[slot][alpha][b][a]. Elsewhere the device forms
+    // the one column of M_alpha a jump needs from V.
+    std::vector<int32_t> gslot;  // [K] slot in Rgen, or -1
+    int n_general = 0;
+    hvec<double> Rgen;           // [n_general][n][N][N]
     std::vector<double> lvlE;    // [K][N]     energy of each level's manifold
     std::vector<int32_t> mfirst; // [K][N]     first level of each level's manifold
     std::vector<int32_t> msize;  // [K][N]     size of each level's manifold
     std::vector<GridMeta> meta;  // [K]
     hvec<double> OT;             // [K-1][N][N] transpose of O_g = V_{g+1}^T V_g: OT[b][a] = O[a][b]
+    // Time-step conditions of Eq. newcond (Sec. IV), each term's minimum over the
+    // grid (ns) and the grid point where it is reached: 2 |H_eff| / |dH_eff/dt|,
+    // 1 / |H_eff|, |lambda / (lambda^2 - dlambda/dt)|.
+    double dt_bound[3] = {0.0, 0.0, 0.0};
+    int dt_bound_at[3] = {0, 0, 0};
 };
 
 struct Inputs {
@@ -98,17 +108,24 @@ struct Inputs {
     int64_t M = 0;
     uint64_t seed = 0;
     int precision = 0;
+    int timing = 0;
     int64_t jcap = 0;
 };
 
 // Returns AQT_OK or an error with a message in *err.
 aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
 
+// Jump amplitudes R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b] of grid point
+// g, out[alpha][a][b], recomputed from the tables' eigenvectors (inspection).
+void jump_amplitudes(const Inputs &in, const Tables &tab, int g, double *out);
+
 // ------------------------------------------------------------- kernels ------
 struct DevTables {
     const double *kdiag, *ehalf, *d2, *G, *lvlE;
-    const void *Rt;     // [g][alpha][b][a]: double (FP64 path) or float
-    const float *Gt32;  // FP32 and tensor-core paths: [g][b][8] stage-one rates, alpha padded to 8
+    const double *Mdiag;  // [g][alpha][N] diagonal of M_alpha
+    const void *V;        // [g][x][a] eigenvectors in the state precision (double or float)
+    const int32_t *gslot; // [g] slot of the general jump tables, -1 at simple grid points
+    const double *Rgen;   // [slot][alpha][b][a] jump amplitudes at general grid points
     const float *ehalf32;
     const int32_t *mfirst, *msize;
     const GridMeta *meta;
@@ -116,8 +133,14 @@ struct DevTables {
     const void *tclvl;  // tensor-core path: float4 [g][N] = (Re, Im of exp(-i K tau), 1 - d2, d2)
 };
 
+// When a jump happens inside a frozen half-step (Sec. IV): at the root of the
+// norm-crossing condition (REFINED), or at the end of the half-step in which
+// the norm fell to the threshold (GRID).
+enum JumpTiming : int { kTimingRefined = 0, kTimingGrid = 1 };
+
 struct RunParams {
     int n, N, K, TT, RA, n_cta;
+    int timing;
     int64_t M;
     uint64_t seed;
     double tau, dt;
@@ -131,12 +154,20 @@ struct RunParams {
     double *obs_sum;               // [K][2]
     double *scratch;               // [n_cta][kScratchSlots][kSlotDouble2 * N][2] jump scratch
     int32_t *status;
+    // Poll limit of the tensor-core kernel's bounded waits between its roles
+    // (the waits also end after about 2 s).
+    long long wait_polls;
+    // Largest |(squared norm after a frame rotation) / (before) - 1| over all
+    // trajectories and steps, as the bits of a non-negative float (atomicMax on
+    // the bits orders like the values); not recorded when null.
+    unsigned int *norm_err;
 };
 
 // Jump scratch per warp (SIMT) or jump slot (tensor-core path), in double2
 // units per level: two FP64 vectors for the general jump operator, then one
 // FP32 state (real, imaginary planes) handed between the epilogue warps.
 constexpr int kSlotDouble2 = 3;
+constexpr long long kDefaultWaitPolls = 1ll << 22;
 constexpr int kScratchSlots = 8;
 
 // Scratch bytes of a run: the jump slots of every CTA, then, for the

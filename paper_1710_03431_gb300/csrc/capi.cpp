@@ -16,8 +16,8 @@
 using namespace aqt;
 
 struct Layout {
-    size_t kdiag, ehalf, ehalf32, d2, G, Gt, R, lvlE, mfirst, msize, meta, OT, tclvl;
-    size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, total;
+    size_t kdiag, ehalf, ehalf32, d2, G, Mdiag, V, gslot, Rgen, lvlE, mfirst, msize, meta, OT, tclvl;
+    size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, norm_err, total;
 };
 
 struct aqt_ctx {
@@ -36,6 +36,8 @@ struct aqt_ctx {
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     bool ran = false;
+    long long wait_polls = kDefaultWaitPolls;
+    size_t uploaded = 0;  // bytes copied to the device by the last aqt_build_tables
 };
 
 namespace {
@@ -101,8 +103,10 @@ void compute_layout(aqt_ctx *c) {
     L.ehalf32 = take(K * N * 2 * 4);
     L.d2 = take(K * N * 8);
     L.G = take(K * n * N * 8);
-    L.Gt = take(in.precision == AQT_PREC_FP64 ? 0 : K * N * 8 * 4);
-    L.R = take(K * n * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
+    L.Mdiag = take(K * n * N * 8);
+    L.V = take(K * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
+    L.gslot = take(K * 4);
+    L.Rgen = take((size_t)c->tab.n_general * n * N * N * 8);
     L.lvlE = take(K * N * 8);
     L.mfirst = take(K * N * 4);
     L.msize = take(K * N * 4);
@@ -116,6 +120,7 @@ void compute_layout(aqt_ctx *c) {
     L.obs_sum = take(K * 2 * 8);
     L.scratch = take(scratch_bytes(c->n_cta, (int)N, c->TT, tc));
     L.status = take(4);
+    L.norm_err = take(4);
     L.total = off;
 }
 
@@ -133,6 +138,84 @@ aqt_status use_device(aqt_ctx *c) {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     return AQT_OK;
+}
+
+// Run parameters over the context's device tables; outputs and scratch point
+// into the workspace (the static-scratch entry point replaces them).
+void fill_params(const aqt_ctx *c, RunParams *p) {
+    const Layout &L = c->lay;
+    const Inputs &in = c->in;
+    *p = RunParams{};
+    p->n = in.n;
+    p->N = 1 << in.n;
+    p->K = in.K;
+    p->TT = c->TT;
+    p->RA = c->RA;
+    p->n_cta = c->n_cta;
+    p->timing = in.timing;
+    p->M = in.M;
+    p->seed = in.seed;
+    p->tau = c->tab.tau;
+    p->dt = c->tab.dt;
+    p->eta_g2 = in.bath.eta_g2;
+    p->omega_c = in.bath.omega_c;
+    p->beta = in.bath.beta;
+    p->tab.kdiag = (const double *)(c->ws + L.kdiag);
+    p->tab.ehalf = (const double *)(c->ws + L.ehalf);
+    p->tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
+    p->tab.d2 = (const double *)(c->ws + L.d2);
+    p->tab.G = (const double *)(c->ws + L.G);
+    p->tab.Mdiag = (const double *)(c->ws + L.Mdiag);
+    p->tab.V = c->ws + L.V;
+    p->tab.gslot = (const int32_t *)(c->ws + L.gslot);
+    p->tab.Rgen = (const double *)(c->ws + L.Rgen);
+    p->tab.lvlE = (const double *)(c->ws + L.lvlE);
+    p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
+    p->tab.msize = (const int32_t *)(c->ws + L.msize);
+    p->tab.meta = (const GridMeta *)(c->ws + L.meta);
+    p->tab.OT = c->ws + L.OT;
+    p->tab.tclvl = c->ws + L.tclvl;
+    p->final_state = (double *)(c->ws + L.final_state);
+    p->jumps = (aqt_jump *)(c->ws + L.jumps);
+    p->jcap = in.jcap;
+    p->jcount = (unsigned long long *)(c->ws + L.jcount);
+    p->obs_part = (double *)(c->ws + L.obs_part);
+    p->obs_sum = (double *)(c->ws + L.obs_sum);
+    p->scratch = (double *)(c->ws + L.scratch);
+    p->status = (int32_t *)(c->ws + L.status);
+    p->norm_err = (unsigned int *)(c->ws + L.norm_err);
+    p->wait_polls = c->wait_polls;
+}
+
+// The host tables (built once per set of inputs): the workspace layout depends
+// on them (the jump amplitudes are kept only at grid points that need them).
+aqt_status ensure_host_tables(aqt_ctx *c) {
+    if (c->tables_built) return AQT_OK;
+    std::string err;
+    aqt_status s = build_tables(c->in, c->tab, &err);
+    if (s != AQT_OK) return fail(c, s, err);
+    c->tables_built = true;
+    return AQT_OK;
+}
+
+// AQT_WDT when the grid step is not well below a term of Eq. newcond (Sec. IV)
+// that applies to the chosen jump timing, AQT_OK otherwise. "Well below":
+// dt <= 0.1 x the term. The 1/|H_eff| term bounds the error of a first-order
+// no-jump step; here the frozen-generator phases are exact, so it is reported
+// (aqt_get_dt_bounds) but not checked. The lambda term bounds the error of a
+// fixed-step jump probability, which only GRID timing makes.
+aqt_status dt_warning(aqt_ctx *c) {
+    const Tables &t = c->tab;
+    static const char *what[3] = {"2|H_eff|/|dH_eff/dt|", "1/|H_eff|", "|lambda/(lambda^2 - dlambda/dt)|"};
+    std::string msg;
+    for (int i = 0; i < 3; ++i) {
+        if (i == 1 || (i == 2 && c->in.timing != AQT_JUMP_GRID)) continue;
+        if (t.dt > 0.1 * t.dt_bound[i])
+            msg += std::string(msg.empty() ? "" : "; ") + "dt = " + std::to_string(t.dt) + " ns is not << " + what[i] +
+                   " = " + std::to_string(t.dt_bound[i]) + " ns (grid point " + std::to_string(t.dt_bound_at[i]) + ")";
+    }
+    if (msg.empty()) return AQT_OK;
+    return fail(c, AQT_WDT, "time-step condition of Eq. newcond: " + msg);
 }
 
 }  // namespace
@@ -162,35 +245,7 @@ aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
     aqt_status s = use_device(c);
     if (s != AQT_OK) return s;
     if (!c->tables_on_device) return fail(c, AQT_EINVAL, "build tables on the device before running");
-    const Layout &L = c->lay;
-    const Inputs &in = c->in;
-    *p = RunParams{};
-    p->n = in.n;
-    p->N = 1 << in.n;
-    p->K = in.K;
-    p->TT = c->TT;
-    p->RA = c->RA;
-    p->n_cta = c->n_cta;
-    p->M = in.M;
-    p->seed = in.seed;
-    p->tau = c->tab.tau;
-    p->dt = c->tab.dt;
-    p->eta_g2 = in.bath.eta_g2;
-    p->omega_c = in.bath.omega_c;
-    p->beta = in.bath.beta;
-    p->tab.kdiag = (const double *)(c->ws + L.kdiag);
-    p->tab.ehalf = (const double *)(c->ws + L.ehalf);
-    p->tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
-    p->tab.d2 = (const double *)(c->ws + L.d2);
-    p->tab.G = (const double *)(c->ws + L.G);
-    p->tab.Rt = c->ws + L.R;
-    p->tab.Gt32 = (const float *)(c->ws + L.Gt);
-    p->tab.lvlE = (const double *)(c->ws + L.lvlE);
-    p->tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
-    p->tab.msize = (const int32_t *)(c->ws + L.msize);
-    p->tab.meta = (const GridMeta *)(c->ws + L.meta);
-    p->tab.OT = c->ws + L.OT;
-    p->tab.tclvl = c->ws + L.tclvl;
+    fill_params(c, p);
     return AQT_OK;
 }
 
@@ -287,15 +342,19 @@ aqt_status aqt_set_grid(aqt_ctx *c, double t_f, int n_grid) {
     return AQT_OK;
 }
 
-aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precision, int64_t jump_capacity) {
+aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precision, int jump_timing,
+                                int64_t jump_capacity) {
     if (!c) return AQT_EINVAL;
     if (M < 1 || M > (int64_t)1 << 31) return fail(c, AQT_EINVAL, "M must be in [1, 2^31]");
     if (precision != AQT_PREC_FP64 && precision != AQT_PREC_FP32 && precision != AQT_PREC_F16SPLIT)
         return fail(c, AQT_EINVAL, "unknown precision");
+    if (jump_timing != AQT_JUMP_REFINED && jump_timing != AQT_JUMP_GRID)
+        return fail(c, AQT_EINVAL, "unknown jump timing");
     if (jump_capacity < 0) return fail(c, AQT_EINVAL, "jump_capacity must be >= 0");
     c->in.M = M;
     c->in.seed = seed;
     c->in.precision = precision;
+    c->in.timing = jump_timing;
     c->in.jcap = jump_capacity;
     c->in.have_traj = true;
     invalidate(c);
@@ -306,6 +365,7 @@ aqt_status aqt_workspace_size(aqt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set ising, schedule, bath, grid and trajectories first");
     aqt_status s = device_shape_check(c);
+    if (s == AQT_OK) s = ensure_host_tables(c);
     if (s != AQT_OK) return s;
     compute_layout(c);
     *bytes = c->lay.total;
@@ -316,6 +376,7 @@ aqt_status aqt_bind_workspace(aqt_ctx *c, void *dptr, size_t bytes) {
     if (!c) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs before binding a workspace");
     aqt_status s = device_shape_check(c);
+    if (s == AQT_OK) s = ensure_host_tables(c);
     if (s != AQT_OK) return s;
     compute_layout(c);
     if (!dptr || ((uintptr_t)dptr & 255)) return fail(c, AQT_EINVAL, "workspace must be 256-byte aligned");
@@ -330,14 +391,11 @@ aqt_status aqt_bind_workspace(aqt_ctx *c, void *dptr, size_t bytes) {
 aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     if (!c) return AQT_EINVAL;
     if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs before building tables");
-    if (!c->tables_built) {
-        std::string err;
-        aqt_status s = build_tables(c->in, c->tab, &err);
-        if (s != AQT_OK) return fail(c, s, err);
-        c->tables_built = true;
-    }
-    if (c->device < 0) return AQT_OK;
-    aqt_status s = use_device(c);
+    aqt_status s = ensure_host_tables(c);
+    if (s != AQT_OK) return s;
+    if (c->device < 0) return dt_warning(c);
+    s = device_shape_check(c);
+    if (s == AQT_OK) s = use_device(c);
     if (s != AQT_OK) return s;
     if (!c->ws) return fail(c, AQT_EINVAL, "bind a workspace before building tables on a device");
     compute_layout(c);
@@ -345,45 +403,50 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const Tables &t = c->tab;
     const Layout &L = c->lay;
-    std::vector<float> e32(t.ehalf.begin(), t.ehalf.end());
+    const size_t N = t.N, K = t.K, NN = N * N;
+    c->uploaded = 0;
     auto put = [&](size_t off, const void *src, size_t bytes) -> cudaError_t {
         if (!bytes) return cudaSuccess;
+        c->uploaded += bytes;
         return cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, st);
     };
+    std::vector<float> e32(t.ehalf.begin(), t.ehalf.end());
     cudaError_t e = cudaSuccess;
     if (!e) e = put(L.kdiag, t.kdiag.data(), t.kdiag.size() * 8);
     if (!e) e = put(L.ehalf, t.ehalf.data(), t.ehalf.size() * 8);
     if (!e) e = put(L.ehalf32, e32.data(), e32.size() * 4);
     if (!e) e = put(L.d2, t.d2.data(), t.d2.size() * 8);
     if (!e) e = put(L.G, t.G.data(), t.G.size() * 8);
-    if (!e && !t.Rt.empty()) e = put(L.R, t.Rt.data(), t.Rt.size() * 8);
-    if (!e && !t.Rt32.empty()) e = put(L.R, t.Rt32.data(), t.Rt32.size() * 4);
-    std::vector<float> gt;
-    if (c->in.precision != AQT_PREC_FP64) {
-        // stage-one rates level-major in FP32, 8 alphas per level (zero past n)
-        const size_t N = t.N, n = t.n, K = t.K;
-        gt.assign(K * N * 8, 0.0f);
-        for (size_t g = 0; g < K; ++g)
-            for (size_t al = 0; al < n; ++al)
-                for (size_t b = 0; b < N; ++b) gt[(g * N + b) * 8 + al] = (float)t.G[(g * n + al) * N + b];
-        if (!e) e = put(L.Gt, gt.data(), gt.size() * 4);
-    }
+    if (!e) e = put(L.Mdiag, t.Mdiag.data(), t.Mdiag.size() * 8);
+    if (!e) e = put(L.gslot, t.gslot.data(), t.gslot.size() * 4);
+    if (!e) e = put(L.Rgen, t.Rgen.data(), t.Rgen.size() * 8);
     if (!e) e = put(L.lvlE, t.lvlE.data(), t.lvlE.size() * 8);
     if (!e) e = put(L.mfirst, t.mfirst.data(), t.mfirst.size() * 4);
     if (!e) e = put(L.msize, t.msize.data(), t.msize.size() * 4);
     if (!e) e = put(L.meta, t.meta.data(), t.meta.size() * sizeof(GridMeta));
+    // eigenvectors (jump columns) and frame rotations in the state precision
+    hvec<float> v32, o32;
+    hvec<__half> o16;
+    std::vector<float> lv;
     if (c->in.precision == AQT_PREC_FP64) {
+        if (!e) e = put(L.V, t.V.data(), t.V.size() * 8);
         if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
-        if (!e) e = cudaStreamSynchronize(st);
-    } else if (c->in.precision == AQT_PREC_F16SPLIT) {
+    } else {
+        v32.resize(K * NN);
+        parallel_rows(K, [&](size_t g) {
+            for (size_t i = 0; i < NN; ++i) v32[g * NN + i] = (float)t.V[g * NN + i];
+        });
+        if (!e) e = put(L.V, v32.data(), v32.size() * 4);
+    }
+    if (c->in.precision == AQT_PREC_F16SPLIT) {
         // A-operand tiles in the order the tensor-core kernel streams them: per grid
         // step, 128-level block h of rows a, and pair of K-blocks (16 levels b
         // each), a 16 KB stage: the hi halves of O[a][b] for the two K-blocks
         // (4 KB each), then the lo halves. Each 4 KB block holds 8x16-byte core
         // matrices: core (a/8, k/8) at ((a/8)*2 + k/8)*128 bytes, row a%8 at 16
         // bytes, column k%8 at 2 bytes (a, k local to the block).
-        const size_t N = t.N, NK = N / 16, K = t.K, MH = N / 128;
-        hvec<__half> o16((K - 1) * N * N * 2);
+        const size_t NK = N / 16, MH = N / 128;
+        o16.resize((K - 1) * NN * 2);
         parallel_rows(K - 1, [&](size_t g) {
             for (size_t h = 0; h < MH; ++h)
                 for (size_t kb = 0; kb < NK; ++kb) {
@@ -391,7 +454,7 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
                     __half *lo = hi + 4096;
                     for (size_t al = 0; al < 128; ++al)
                         for (size_t k = 0; k < 16; ++k) {
-                            const double o = t.OT[g * N * N + (kb * 16 + k) * N + 128 * h + al];
+                            const double o = t.OT[g * NN + (kb * 16 + k) * N + 128 * h + al];
                             const __half hh = __float2half_rn((float)o);
                             const __half ll = __float2half_rn((float)(o - (double)__half2float(hh)));
                             const size_t off = ((al >> 3) * 2 + (k >> 3)) * 64 + (al & 7) * 8 + (k & 7);
@@ -400,7 +463,7 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
                         }
                 }
         });
-        std::vector<float> lv(K * N * 4);
+        lv.resize(K * N * 4);
         for (size_t g = 0; g < K; ++g)
             for (size_t a = 0; a < N; ++a) {
                 const double im = t.kdiag[(g * N + a) * 2 + 1];
@@ -411,15 +474,17 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
             }
         if (!e) e = put(L.OT, o16.data(), o16.size() * sizeof(__half));
         if (!e) e = put(L.tclvl, lv.data(), lv.size() * 4);
-        if (!e) e = cudaStreamSynchronize(st);
-    } else {
-        std::vector<float> o32(t.OT.begin(), t.OT.end());
+    } else if (c->in.precision == AQT_PREC_FP32) {
+        o32.resize((K - 1) * NN);
+        parallel_rows(K - 1, [&](size_t g) {
+            for (size_t i = 0; i < NN; ++i) o32[g * NN + i] = (float)t.OT[g * NN + i];
+        });
         if (!e) e = put(L.OT, o32.data(), o32.size() * 4);
-        if (!e) e = cudaStreamSynchronize(st);  // host staging buffers go out of scope
     }
+    if (!e) e = cudaStreamSynchronize(st);  // host staging buffers go out of scope
     if (e) return cuda_fail(c, e, "table upload");
     c->tables_on_device = true;
-    return AQT_OK;
+    return dt_warning(c);
 }
 
 aqt_status aqt_run(aqt_ctx *c, void *stream) {
@@ -431,44 +496,11 @@ aqt_status aqt_run(aqt_ctx *c, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(c->ws + L.jcount, 0, 8, st);
     if (!e) e = cudaMemsetAsync(c->ws + L.status, 0, 4, st);
+    if (!e) e = cudaMemsetAsync(c->ws + L.norm_err, 0, 4, st);
     if (e) return cuda_fail(c, e, "cudaMemsetAsync");
-    RunParams p{};
-    const Inputs &in = c->in;
-    p.n = in.n;
-    p.N = 1 << in.n;
-    p.K = in.K;
-    p.TT = c->TT;
-    p.RA = c->RA;
-    p.n_cta = c->n_cta;
-    p.M = in.M;
-    p.seed = in.seed;
-    p.tau = c->tab.tau;
-    p.dt = c->tab.dt;
-    p.eta_g2 = in.bath.eta_g2;
-    p.omega_c = in.bath.omega_c;
-    p.beta = in.bath.beta;
-    p.tab.kdiag = (const double *)(c->ws + L.kdiag);
-    p.tab.ehalf = (const double *)(c->ws + L.ehalf);
-    p.tab.ehalf32 = (const float *)(c->ws + L.ehalf32);
-    p.tab.d2 = (const double *)(c->ws + L.d2);
-    p.tab.G = (const double *)(c->ws + L.G);
-    p.tab.Rt = c->ws + L.R;
-    p.tab.Gt32 = (const float *)(c->ws + L.Gt);
-    p.tab.lvlE = (const double *)(c->ws + L.lvlE);
-    p.tab.mfirst = (const int32_t *)(c->ws + L.mfirst);
-    p.tab.msize = (const int32_t *)(c->ws + L.msize);
-    p.tab.meta = (const GridMeta *)(c->ws + L.meta);
-    p.tab.OT = c->ws + L.OT;
-    p.tab.tclvl = c->ws + L.tclvl;
-    p.final_state = (double *)(c->ws + L.final_state);
-    p.jumps = (aqt_jump *)(c->ws + L.jumps);
-    p.jcap = in.jcap;
-    p.jcount = (unsigned long long *)(c->ws + L.jcount);
-    p.obs_part = (double *)(c->ws + L.obs_part);
-    p.obs_sum = (double *)(c->ws + L.obs_sum);
-    p.scratch = (double *)(c->ws + L.scratch);
-    p.status = (int32_t *)(c->ws + L.status);
-    int ce = launch_run(p, in.precision, stream, c->smem);
+    RunParams p;
+    fill_params(c, &p);
+    int ce = launch_run(p, c->in.precision, stream, c->smem);
     if (ce) return cuda_fail(c, (cudaError_t)ce, "kernel launch");
     c->stream = st;
     c->ran = true;
@@ -514,6 +546,37 @@ aqt_status aqt_get_observable_sums(aqt_ctx *c, double *sum_x, double *sum_x2) {
         sum_x[g] = buf[2 * g];
         sum_x2[g] = buf[2 * g + 1];
     }
+    return AQT_OK;
+}
+
+aqt_status aqt_set_wait_limit(aqt_ctx *c, int64_t polls) {
+    if (!c) return AQT_EINVAL;
+    if (polls < 0 || polls > kDefaultWaitPolls) return fail(c, AQT_EINVAL, "poll limit must be in [0, 2^22]");
+    c->wait_polls = polls;
+    return AQT_OK;
+}
+
+aqt_status aqt_get_dt_bounds(aqt_ctx *c, double *bounds, int32_t *at) {
+    if (!c || !bounds) return AQT_EINVAL;
+    if (!c->tables_built) return fail(c, AQT_EINVAL, "build tables first");
+    for (int i = 0; i < 3; ++i) {
+        bounds[i] = c->tab.dt_bound[i];
+        if (at) at[i] = c->tab.dt_bound_at[i];
+    }
+    return AQT_OK;
+}
+
+aqt_status aqt_get_rotation_error(aqt_ctx *c, double *max_rel) {
+    if (!c || !max_rel) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "run first");
+    unsigned int bits = 0;
+    cudaError_t e = cudaMemcpy(&bits, c->ws + c->lay.norm_err, 4, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "norm error readback");
+    float v;
+    std::memcpy(&v, &bits, 4);
+    *max_rel = v;
     return AQT_OK;
 }
 
@@ -597,14 +660,7 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
         case 0: std::copy_n(&t.evals[g * N], N, out); break;
         case 1: std::copy_n(&t.kdiag[g * N * 2], N * 2, out); break;
         case 2: std::copy_n(&t.G[g * n * N], n * N, out); break;
-        case 3:
-            for (size_t al = 0; al < n; ++al)
-                for (size_t a = 0; a < N; ++a)
-                    for (size_t b = 0; b < N; ++b) {
-                        const size_t i = (g * n + al) * NN + b * N + a;
-                        out[al * NN + a * N + b] = t.Rt.empty() ? (double)t.Rt32[i] : t.Rt[i];
-                    }
-            break;
+        case 3: jump_amplitudes(c->in, t, (int)g, out); break;
         case 4:
             for (size_t a = 0; a < N; ++a)
                 for (size_t b = 0; b < N; ++b) out[a * N + b] = t.OT[g * NN + b * N + a];
@@ -616,6 +672,10 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
             out[1] = t.meta[g].gs_size;
             out[2] = t.meta[g].simple;
             out[3] = t.meta[g].tol;
+            break;
+        case 8:
+            out[0] = t.n_general;
+            out[1] = (double)c->uploaded;
             break;
         default: return fail(c, AQT_EINVAL, "unknown table");
     }

@@ -6,23 +6,29 @@
 // (K diagonal), and a jump happens when the clock ell + log1p(delta(t)) falls
 // to the threshold log r. The warp that owns the trajectory holds its state in
 // registers (level a = 32 j + lane in slot j), finds the crossing time by
-// Newton's method from the left (the function is convex and decreasing, so
-// the iterates never overshoot), draws the channel with the probabilities of
-// App. B.1 (Eq. Pi(t)), applies the Bohr-class operator (Eq. jump),
-// renormalises, draws a new threshold and finishes the half-step, possibly
-// jumping again.
+// Newton's method (the function is convex and decreasing), draws the channel
+// with the probabilities of App. B.1 (Eq. Pi(t)), applies the Bohr-class
+// operator (Eq. jump), renormalises, draws a new threshold and finishes the
+// half-step, possibly jumping again.
 //
-// The clock is FP64. The per-level arithmetic runs in the state's precision T
-// (double for the FP64 path; float for the FP32 and tensor-core paths, whose
-// states are FP32); writing the norm decay as expm1 terms keeps its relative
+// Precision: the state and its no-jump propagation are in the state's
+// precision T (double on the FP64 path; float on the FP32 and tensor-core
+// paths). Everything that decides a jump is FP64 on every path: the clock,
+// the decay sums delta(t) formed from the populations |c_a|^2 (exact products
+// of the state's entries), the crossing time (for float states a cheap FP32
+// Newton start, then Newton on the FP64 function), and the cumulative sums of
+// both channel draws. Writing the decay as expm1 terms keeps its relative
 // accuracy however small it is.
 //
 // Fast path (every manifold a single level and every Bohr class of nonzero
-// frequency a single level pair, the generic case once s > 0): the class
-// operator maps the source level to the target level alone, or, at zero
-// frequency, scales each level by its diagonal amplitude. Otherwise the state
-// goes to per-warp scratch and a general FP64 routine draws and applies the
-// jump over degenerate manifolds and multi-pair classes.
+// frequency a single level pair, the generic case once s > 0): stage one
+// picks (alpha, source b) from the FP64 rates G; stage two needs column b of
+// M_alpha = V^T sz_alpha V, which the warp forms from the eigenvector table
+// (O(N^2) per jump), weighted by gamma(E_b - E_a) computed in FP64. The class
+// operator then maps the source level to the target level alone, or, at zero
+// frequency, scales each level by the diagonal of M_alpha. Other grid points
+// go through a general FP64 routine over degenerate manifolds and
+// multi-pair classes, with the full jump amplitudes of those grid points.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -68,15 +74,6 @@ static __device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
 static __device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
 static __device__ __forceinline__ void m_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
 static __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sincos(x, s, c); }
-
-// Newton stops once a step is this small relative to t: the error left after
-// it is of the order of its square.
-template <typename T>
-static __device__ __forceinline__ T newton_rel();
-template <>
-__device__ __forceinline__ float newton_rel<float>() { return 1e-3f; }
-template <>
-__device__ __forceinline__ double newton_rel<double>() { return 1e-7; }
 
 // v[j] for a warp-uniform runtime j, without indexing the register array.
 template <typename T, int NPL>
@@ -134,7 +131,7 @@ static __device__ __forceinline__ int reg_pick(const T (&w)[NPL], T target, int 
 // operator A_{alpha, omega*} (Eq. jump) in FP64. c64 holds the normalised
 // state (N entries) and receives the normalised post-jump state; y64 is
 // scratch. Returns alpha (or -1 on a numeric failure), source and target.
-template <typename RT>
+using RT = double;
 static __device__ int general_draw_apply(const RunParams &p, int g, double u1, double u2, double2 *c64, double2 *y64,
                                          int lane, int *bsrc_out, int *adst_out) {
     const int N = p.N, n = p.n;
@@ -142,7 +139,9 @@ static __device__ int general_draw_apply(const RunParams &p, int g, double u1, d
     const int32_t *mfirst = p.tab.mfirst + (size_t)g * N;
     const int32_t *msize = p.tab.msize + (size_t)g * N;
     const GridMeta meta = p.tab.meta[g];
-    const RT *Rg = static_cast<const RT *>(p.tab.Rt) + (size_t)g * n * N * N;  // [alpha][b][a]
+    const int slot = p.tab.gslot[g];
+    if (slot < 0) return -1;  // tables missing for this grid point
+    const RT *Rg = p.tab.Rgen + (size_t)slot * n * N * N;  // [alpha][b][a]
     const double *Gg = p.tab.G + (size_t)g * n * N;
     // stage-one weight of unit (alpha, manifold starting at b); -1 marks a
     // degenerate manifold, whose weight the warp computes with manifold_w
@@ -314,6 +313,39 @@ static __device__ int general_draw_apply(const RunParams &p, int g, double u1, d
     return al_s;
 }
 
+// Gamma of the Ohmic bath (Sec. V): 2 pi eta g^2 w e^{-|w|/w_c} / (1 - e^{-beta w}),
+// with its limit 2 pi eta g^2 / beta at w = 0; FP64.
+static __device__ __forceinline__ double bath_gamma(const RunParams &p, double w) {
+    if (w == 0.0) return 2.0 * 3.14159265358979323846 * p.eta_g2 / p.beta;
+    return 2.0 * 3.14159265358979323846 * p.eta_g2 * w * exp(-fabs(w) / p.omega_c) / (-expm1(-p.beta * w));
+}
+
+// Column b of M_alpha = V^T sz_alpha V at grid point g for the levels a = 32 j
+// + lane of this lane: M[a][b] = delta_ab - 2 sum over basis states x with bit
+// alpha set of V[x][a] V[x][b] (sz_alpha = 1 - 2 P_alpha). V in the state's
+// precision, accumulated in it.
+template <typename T, int NPL>
+static __device__ __forceinline__ void m_column(const RunParams &p, int g, int al, int b, int lane, T (&m)[NPL]) {
+    const int N = p.N;
+    const T *Vg = static_cast<const T *>(p.tab.V) + (size_t)g * N * N;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) m[j] = T(0);
+    const int lo_mask = (1 << al) - 1;
+#pragma unroll 4
+    for (int i = 0; i < N / 2; ++i) {
+        const int x = ((i >> al) << (al + 1)) | (1 << al) | (i & lo_mask);
+        const T *row = Vg + (size_t)x * N;
+        const T vb = row[b];
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const int a = 32 * j + lane;
+            if (a < N) m[j] = fma(row[a], vb, m[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) m[j] = (32 * j + lane == b ? T(1) : T(0)) - T(2) * m[j];
+}
+
 // One frozen half-step of one trajectory that may cross its threshold,
 // resolved by one warp with the state in registers (NPL levels per lane,
 // 32 NPL >= N). sre/sim: the state, level a at [a * stride] (normalised or
@@ -321,16 +353,16 @@ static __device__ int general_draw_apply(const RunParams &p, int g, double u1, d
 // logr, nj: the trajectory's clock, log threshold and jump count (the same on
 // every lane). slow: 2N double2 of per-warp scratch for the general jump.
 // klev (FP32 paths, optional): (Re K_aa, 2 Im K_aa) of grid point g staged in
-// shared memory; otherwise the FP64 table is read.
+// shared memory for the FP32 propagation; otherwise the FP64 table is read.
 template <typename T, int NPL>
 static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g, int half, int64_t traj, T *sre,
                                                       T *sim, int stride, double &ell, double &logr, int &nj,
                                                       int lane, double2 *slow, const float2 *klev = nullptr) {
+    constexpr bool f32 = std::is_same<T, float>::value;
     const int N = p.N, n = p.n;
     const GridMeta meta = p.tab.meta[g];
     const double *kd = p.tab.kdiag + (size_t)g * N * 2;
     const double *Gg = p.tab.G + (size_t)g * n * N;
-    const T *Rg = static_cast<const T *>(p.tab.Rt) + (size_t)g * n * N * N;  // [alpha][b][a]
     const bool fast = meta.simple && !meta.degenerate;
     T cr[NPL], ci[NPL];
 #pragma unroll
@@ -340,20 +372,27 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         cr[j] = v ? sre[(size_t)a * stride] : T(0);
         ci[j] = v ? sim[(size_t)a * stride] : T(0);
     }
-    // diagonal of K per level (re, 2 im), re-read from the cache where used to
-    // keep registers free
+    // diagonal of K per level (re, 2 im) in the state's precision, re-read from
+    // the cache where used to keep registers free
     auto kre = [&](int j) -> T {
         const int a = 32 * j + lane;
-        if constexpr (std::is_same<T, float>::value)
+        if constexpr (f32)
             if (klev) return a < N ? klev[a].x : 0.0f;
         return a < N ? (T)kd[2 * a] : T(0);
     };
     auto kim2 = [&](int j) -> T {
         const int a = 32 * j + lane;
-        if constexpr (std::is_same<T, float>::value)
+        if constexpr (f32)
             if (klev) return a < N ? klev[a].y : 0.0f;
         return a < N ? (T)(2.0 * kd[2 * a + 1]) : T(0);
     };
+    // 2 Im K_aa in FP64 (decay sums of the clock)
+    auto kim2d = [&](int j) -> double {
+        const int a = 32 * j + lane;
+        return a < N ? 2.0 * kd[2 * a + 1] : 0.0;
+    };
+    // |c_a|^2 in FP64 (exact for float entries)
+    auto pop = [&](int j) -> double { return (double)cr[j] * (double)cr[j] + (double)ci[j] * (double)ci[j]; };
     // c <- c exp(-i K t) / |.|; false if the norm is not positive and finite
     auto advance = [&](T t) -> bool {
         T s = T(0);
@@ -377,16 +416,30 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         }
         return true;
     };
-    // delta(t) of the normalised state and its derivative
-    auto decay = [&](T t, T *d1) -> T {
-        T d = T(0), e1 = T(0);
+    // delta(t) of the normalised state and its derivative, FP64
+    auto decay64 = [&](double t, double *d1) -> double {
+        double d = 0.0, e1 = 0.0;
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
-            const T q = cr[j] * cr[j] + ci[j] * ci[j];
-            const T x = kim2(j);
-            const T e = m_expm1(x * t);
+            const double q = pop(j), x = kim2d(j);
+            const double e = expm1(x * t);
             d += q * e;
-            e1 += q * x * (e + T(1));
+            e1 += q * x * (e + 1.0);
+        }
+        warp_sum2(d, e1);
+        *d1 = e1;
+        return d;
+    };
+    // the same in single precision (a cheap start for the root of float states)
+    auto decay32 = [&](float t, float *d1) -> float {
+        float d = 0.0f, e1 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const float q = (float)(cr[j] * cr[j] + ci[j] * ci[j]);
+            const float x = (float)kim2(j);
+            const float e = expm1f(x * t);
+            d += q * e;
+            e1 += q * x * (e + 1.0f);
         }
         warp_sum2(d, e1);
         *d1 = e1;
@@ -396,32 +449,56 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     double ell0 = ell;
     double tau_rem = p.tau;
     const double t_half0 = half == 0 ? g * p.dt - p.tau : g * p.dt;
-    T dend = T(0);
+    double dend = 0.0;
     for (int it = 0; ok; ++it) {
-        T dd;
-        dend = decay((T)tau_rem, &dd);
+        double dd;
+        dend = decay64(tau_rem, &dd);
         const double C = ell0 - logr;  // > 0 until the threshold is reached
-        if (C + (double)m_log1p(dend) > 0.0) break;
+        if (C + log1p(dend) > 0.0) break;
         if (it >= kMaxJumpsPerHalf) {
             ok = false;
             break;
         }
-        // --- crossing time: Newton from the left on C + log1p(delta(t)) ------------
-        const T Ct = (T)C;
-        T t = T(0);
-        for (int k = 0; k < 40; ++k) {
-            T d1;
-            const T d = decay(t, &d1);
-            const T phi = Ct + m_log1p(d);
-            if (!(phi > T(0)) || !(d1 < T(0))) break;
-            const T step = -phi * (T(1) + d) / d1;
-            T tn = t + step;
-            if (tn > (T)tau_rem) tn = (T)tau_rem;
-            if (!(tn > t)) break;
-            t = tn;
-            if (step <= newton_rel<T>() * t) break;
+        // --- crossing time --------------------------------------------------------------
+        double t = tau_rem;  // GRID timing: the end of the half-step
+        if (p.timing == kTimingRefined) {
+            t = 0.0;
+            if constexpr (f32) {
+                // FP32 Newton from the left to ~1e-3 relative
+                const float Cf = (float)C;
+                float tf = 0.0f;
+                for (int k = 0; k < 40; ++k) {
+                    float d1;
+                    const float d = decay32(tf, &d1);
+                    const float phi = Cf + log1pf(d);
+                    if (!(phi > 0.0f) || !(d1 < 0.0f)) break;
+                    const float step = -phi * (1.0f + d) / d1;
+                    float tn = tf + step;
+                    if (tn > (float)tau_rem) tn = (float)tau_rem;
+                    if (!(tn > tf)) break;
+                    tf = tn;
+                    if (step <= 1e-3f * tf) break;
+                }
+                t = (double)tf;
+            }
+            // Newton on the FP64 function (from either side: convexity brings an
+            // iterate right of the root back to its left in one step)
+            for (int k = 0; k < 60; ++k) {
+                double d1;
+                const double d = decay64(t, &d1);
+                const double phi = C + log1p(d);
+                if (phi == 0.0 || !(d1 < 0.0)) break;
+                if (!f32 && !(phi > 0.0)) break;
+                const double step = -phi * (1.0 + d) / d1;
+                double tn = t + step;
+                if (tn > tau_rem) tn = tau_rem;
+                if (tn < 0.0) tn = 0.0;
+                if (tn == t) break;
+                t = tn;
+                if (fabs(step) <= 1e-7 * t) break;
+            }
         }
-        if (!advance(t)) {
+        if (!advance((T)t)) {
             ok = false;
             break;
         }
@@ -431,112 +508,68 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         const double u1 = uniform01(rnd.x[0]), u2 = uniform01(rnd.x[1]), u3 = uniform01(rnd.x[2]);
         int al = -1, bsrc = -1, adst = -1;
         if (fast) {
-            T qv[NPL];
+            double qv[NPL];
 #pragma unroll
-            for (int j = 0; j < NPL; ++j) qv[j] = cr[j] * cr[j] + ci[j] * ci[j];
-            // stage one over units (alpha, b) in that order
-            T total = T(0);
-            T cum = T(0), cum_last = T(0);
+            for (int j = 0; j < NPL; ++j) qv[j] = pop(j);
+            // stage one over units (alpha, b) in that order. The total rate is
+            // sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2 2 Im K_bb, so the
+            // walk over alpha stops at the first alpha whose cumulative sum passes
+            // the target, one warp sum per alpha visited.
+            double total = 0.0, cum = 0.0, cum_last = 0.0;
             int last = -1;
-            if constexpr (std::is_same<T, float>::value) {
-                // all per-alpha totals in one pass over the level-major FP32 rates
-                // (8 alphas per level, two float4)
-                const float4 *gt = reinterpret_cast<const float4 *>(p.tab.Gt32) + (size_t)g * N * 2;
-                float S8[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) S8[k] = 0.0f;
+            for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2d(j);
+            total = warp_sum(total);
+            const double target = u1 * total;
+            for (int a_ = 0; a_ < n && al < 0; ++a_) {
+                double acc = 0.0;
 #pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int b = 32 * j + lane;
-                    if (b < N) {
-                        const float4 x = gt[2 * b], y = gt[2 * b + 1];
-                        S8[0] = fmaf(qv[j], x.x, S8[0]);
-                        S8[1] = fmaf(qv[j], x.y, S8[1]);
-                        S8[2] = fmaf(qv[j], x.z, S8[2]);
-                        S8[3] = fmaf(qv[j], x.w, S8[3]);
-                        S8[4] = fmaf(qv[j], y.x, S8[4]);
-                        S8[5] = fmaf(qv[j], y.y, S8[5]);
-                        S8[6] = fmaf(qv[j], y.z, S8[6]);
-                        S8[7] = fmaf(qv[j], y.w, S8[7]);
-                    }
+                    if (b < N) acc += qv[j] * Gg[(size_t)a_ * N + b];
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) S8[k] += __shfl_xor_sync(0xffffffffu, S8[k], o);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) total += S8[k];
-                const T target = (T)u1 * total;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (al < 0 && k < n) {
-                        if (S8[k] > 0.0f) {
-                            last = k;
-                            cum_last = cum;
-                        }
-                        if (S8[k] > 0.0f && cum + S8[k] > target) al = k;
-                        else cum += S8[k];
-                    }
-            } else {
-                // The total rate is sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2
-                // 2 Im K_bb, so the walk over alpha stops at the first alpha whose
-                // cumulative sum passes the target, one warp sum per alpha visited.
-#pragma unroll
-                for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2(j);
-                total = warp_sum(total);
-                const T target = (T)u1 * total;
-                for (int a_ = 0; a_ < n && al < 0; ++a_) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int j = 0; j < NPL; ++j) {
-                        const int b = 32 * j + lane;
-                        if (b < N) acc += qv[j] * (T)Gg[(size_t)a_ * N + b];
-                    }
-                    acc = warp_sum(acc);
-                    if (acc > T(0)) {
-                        last = a_;
-                        cum_last = cum;
-                    }
-                    if (acc > T(0) && cum + acc > target) al = a_;
-                    else cum += acc;
+                acc = warp_sum(acc);
+                if (acc > 0.0) {
+                    last = a_;
+                    cum_last = cum;
                 }
+                if (acc > 0.0 && cum + acc > target) al = a_;
+                else cum += acc;
             }
-            const T target = (T)u1 * total;
             if (al < 0) {  // rounding at the top of the distribution
                 al = last;
                 cum = cum_last;
             }
             if (al >= 0) {
-                T w[NPL];
+                double w[NPL];
 #pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int b = 32 * j + lane;
-                    if constexpr (std::is_same<T, float>::value)
-                        w[j] = b < N ? qv[j] * p.tab.Gt32[((size_t)g * N + b) * 8 + al] : 0.0f;  // cached by stage one
-                    else
-                        w[j] = b < N ? qv[j] * (T)Gg[(size_t)al * N + b] : T(0);
+                    w[j] = b < N ? qv[j] * Gg[(size_t)al * N + b] : 0.0;
                 }
                 bsrc = reg_pick(w, target - cum, lane);
             }
             if (bsrc >= 0) {
-                // stage two: target a with weight R_alpha[a][bsrc]^2 (source row of Rt)
-                const T *row = Rg + ((size_t)al * N + bsrc) * N;
-                T r[NPL], w[NPL], tot2 = T(0);
+                // stage two: target a with weight gamma(E_b - E_a) M_alpha[a][b]^2
+                T m[NPL];
+                m_column<T, NPL>(p, g, al, bsrc, lane, m);
+                const double *lvlE = p.tab.lvlE + (size_t)g * N;
+                const double eb = lvlE[bsrc];
+                double w[NPL], tot2 = 0.0;
 #pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int a = 32 * j + lane;
-                    r[j] = a < N ? row[a] : T(0);
-                    w[j] = r[j] * r[j];
+                    w[j] = a < N ? bath_gamma(p, eb - lvlE[a]) * ((double)m[j] * (double)m[j]) : 0.0;
                     tot2 += w[j];
                 }
                 tot2 = warp_sum(tot2);
-                adst = reg_pick(w, (T)u2 * tot2, lane);
+                adst = reg_pick(w, u2 * tot2, lane);
                 if (adst >= 0 && adst != bsrc) {
                     // nonzero frequency: the class is the single pair (adst <- bsrc), so
-                    // the normalised result is sign(R[adst][bsrc]) c_bsrc / |c_bsrc| on adst
+                    // the normalised result is sign(M[adst][bsrc]) c_bsrc / |c_bsrc| on adst
                     const T br = __shfl_sync(0xffffffffu, reg_at(cr, bsrc >> 5), bsrc & 31);
                     const T bi = __shfl_sync(0xffffffffu, reg_at(ci, bsrc >> 5), bsrc & 31);
-                    const T ra = __shfl_sync(0xffffffffu, reg_at(r, adst >> 5), adst & 31);
+                    const T ra = __shfl_sync(0xffffffffu, reg_at(m, adst >> 5), adst & 31);
                     const T m2 = br * br + bi * bi;
                     if (m2 > T(0)) {
                         const T f = (ra < T(0) ? T(-1) : T(1)) * m_rsqrt(m2);
@@ -550,13 +583,13 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
                         al = -1;
                     }
                 } else if (adst >= 0) {
-                    // zero frequency: every level pairs with itself, y_a = R_alpha[a][a] c_a
-                    const T *Ra = Rg + (size_t)al * N * N;
+                    // zero frequency: every level pairs with itself, y_a = sqrt(gamma(0)) M_alpha[a][a] c_a
+                    const double *Md = p.tab.Mdiag + ((size_t)g * n + al) * N;
                     T s = T(0);
 #pragma unroll
                     for (int j = 0; j < NPL; ++j) {
                         const int a = 32 * j + lane;
-                        const T d = a < N ? Ra[(size_t)a * N + a] : T(0);
+                        const T d = a < N ? (T)Md[a] : T(0);
                         cr[j] *= d;
                         ci[j] *= d;
                         s += cr[j] * cr[j] + ci[j] * ci[j];
@@ -582,7 +615,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
                 if (a < N) slow[a] = make_double2((double)cr[j], (double)ci[j]);
             }
             __syncwarp();
-            al = general_draw_apply<T>(p, g, u1, u2, slow, slow + N, lane, &bsrc, &adst);
+            al = general_draw_apply(p, g, u1, u2, slow, slow + N, lane, &bsrc, &adst);
 #pragma unroll
             for (int j = 0; j < NPL; ++j) {
                 const int a = 32 * j + lane;
@@ -608,7 +641,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
                 rec.alpha = al;
                 rec.src = bsrc;
                 rec.dst = p.tab.mfirst[(size_t)g * N + adst];
-                rec.t = t_half0 + (p.tau - tau_rem) + (double)t;
+                rec.t = t_half0 + (p.tau - tau_rem) + t;
                 rec.omega = lvlE[bsrc] - lvlE[adst];
                 p.jumps[idx] = rec;
             }
@@ -616,7 +649,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         __syncwarp();
         logr = log(u3);
         ell0 = 0.0;
-        tau_rem -= (double)t;
+        tau_rem -= t;
     }
     if (!ok && lane == 0) atomicOr(p.status, kStatusNumeric);
     // finish the half-step without further jumps
@@ -629,7 +662,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
             sim[(size_t)a * stride] = ci[j];
         }
     }
-    ell = ell0 + (double)m_log1p(dend);
+    ell = ell0 + log1p(dend);
     __syncwarp();
 }
 

@@ -67,10 +67,12 @@ __device__ __forceinline__ const float *ehalf_table<float>(const RunParams &p) {
 template <>
 __device__ __forceinline__ const double *ehalf_table<double>(const RunParams &p) { return p.tab.ehalf; }
 
-// One trajectory's renormalisation, frozen half-step and crossing check.
+// One trajectory's renormalisation, frozen half-step and crossing check. The
+// state is normalised before each rotation, so after it (half = 0) nu - 1 is
+// the rotation's own relative norm error, kept in *nerr.
 template <typename R>
 __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t traj, R *cre, R *cim, int LD,
-                          const R *eh, const double *d2s, Scalars sc, double2 *c64, int lane) {
+                          const R *eh, const double *d2s, Scalars sc, double2 *c64, int lane, float *nerr) {
     const int N = p.N;
     double nu = 0.0, f = 0.0;
     for (int a = lane; a < N; a += 32) {
@@ -85,6 +87,7 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
         if (lane == 0) atomicOr(p.status, kStatusNumeric);
         return;
     }
+    if (half == 0 && g > 0) *nerr = fmaxf(*nerr, (float)fabs(nu - 1.0));
     f /= nu;
     const double ell = sc.ell[t], logr = sc.logr[t];
     const double ell_new = ell + log(f);
@@ -176,10 +179,11 @@ __global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
             p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = s2;
         }
     };
+    float nerr = 0.0f;
     auto half_all = [&](int g, int half) {
         for (int t = warp; t < TT; t += kWarps) {
             if (t0 + t >= p.M) continue;
-            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, lane);
+            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, lane, &nerr);
         }
     };
 
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
         observe(g, p.tab.meta[g].gs_size);
         if (g < K - 1) half_all(g, 1);
     }
+    if (p.norm_err && lane == 0) atomicMax(p.norm_err, __float_as_uint(nerr));
     __syncthreads();
     for (int i = tid; i < N * TT; i += kThreads) {
         const int t = i / N, a = i % N;

@@ -62,12 +62,6 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far above any leg
 // wait sites, reported as status bits 8.. next to kStatusTimeout
 enum : int { kSiteSlot = 0, kSiteDrain, kSiteBReady, kSiteFull, kSiteDFull, kSiteAbort };
 
-__device__ __forceinline__ float warp_sumf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -97,15 +91,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Bounded wait (poll count and wall time, since one try_wait may suspend the
 // thread for a while): false, with the abort flag set and the site recorded,
-// when the limit expires.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *status, int site) {
+// when the limit expires; false at once when another role has aborted. polls:
+// the poll limit (the run's setting; 0 makes the wait expire without polling).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *status, int site,
+                          long long polls) {
     const unsigned long long t0 = global_ns();
-    for (long long i = 0; i < kWaitLimit; ++i) {
+    for (long long i = 0; i < polls; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
         if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) break;
     }
     *abort_flag = 1;
+    atomicOr(status, kStatusTimeout | (1 << (8 + site)));
+    return false;
+}
+
+// Wait for work this thread itself put in flight (its bulk copies), also after
+// an abort, with the fixed limits: false, with the site recorded, if it expires.
+__device__ bool mbar_drain(uint32_t bar, uint32_t parity, int32_t *status, int site) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) break;
+    }
     atomicOr(status, kStatusTimeout | (1 << (8 + site)));
     return false;
 }
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 for (int s = 0; s < MH * NK / 2; ++s, ++it) {
                     const int slot = (int)(it % kStages);
                     if (it >= kStages && !mbar_wait(bar_empty + 8 * slot, (uint32_t)(((it / kStages) - 1) & 1),
-                                                    S.abort_flag, p.status, kSiteSlot)) {
+                                                    S.abort_flag, p.status, kSiteSlot, p.wait_polls)) {
                         run = false;
                         break;
                     }
@@ -424,10 +432,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                              stage_bytes, bar_full + 8 * slot);
                 }
             }
-            // drain: wait (bounded) for the copies still in flight
+            // drain: wait (bounded) for the copies still in flight, also after an
+            // abort (the shared memory they write must outlive them)
             for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
-                if (!mbar_wait(bar_full + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), S.abort_flag,
-                               p.status, kSiteDrain))
+                if (!mbar_drain(bar_full + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), p.status, kSiteDrain))
                     break;
         }
     } else if (warp == 1) {
@@ -455,7 +463,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     for (int kp = 0; kp < NK / 2; ++kp, ++it) {
                         if (h == 0 && (kp == 0 || kp == NK / 4)) {
                             if (!mbar_wait(kp == 0 ? bar_rowsA : bar_rowsB, (uint32_t)((g - 1) & 1), S.abort_flag,
-                                           p.status, kSiteBReady)) {
+                                           p.status, kSiteBReady, p.wait_polls)) {
                                 run = false;
                                 break;
                             }
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         }
                         const int slot = (int)(it % kStages);
                         if (!mbar_wait(bar_full + 8 * slot, (uint32_t)((it / kStages) & 1), S.abort_flag, p.status,
-                                       kSiteFull)) {
+                                       kSiteFull, p.wait_polls)) {
                             run = false;
                             break;
                         }
@@ -595,13 +603,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         }
         // observable at s_0 (every active trajectory is in the ground state)
         if (e == 0) {
-            float sx = 0.f, sx2 = 0.f;
+            double sx = 0.0, sx2 = 0.0;
             for (int t = lane; t < TT; t += 32) {
-                sx += S.x[t];
-                sx2 += S.x[t] * S.x[t];
+                const double x = S.x[t];
+                sx += x;
+                sx2 += x * x;
             }
-            sx = warp_sumf(sx);
-            sx2 = warp_sumf(sx2);
+            warp_sum2(sx, sx2);
             if (lane == 0) {
                 p.obs_part[((size_t)blockIdx.x * K) * 2] = sx;
                 p.obs_part[((size_t)blockIdx.x * K) * 2 + 1] = sx2;
@@ -620,6 +628,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             for (int h = 0; h < MH; ++h) Lnext[h] = lvl[(size_t)1 * N + 128 * h + 32 * q + lane];
             gs_next = p.tab.meta[1].gs_size;
         }
+        float nerr = 0.0f;  // this thread's trajectory: largest relative norm change of a rotation
         for (int g = 1; g < K; ++g) {
             const bool last = g == K - 1;
             const int gs = gs_next;
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 // (a bounded wait can expire for one thread only)
                 if (etid == 0)
                     *S.epi_ok = mbar_wait(nph == 2 && ph == 0 ? bar_b1lo : bar_dfull, (uint32_t)((g - 1) & 1),
-                                          S.abort_flag, p.status, kSiteDFull) ? 1 : 0;
+                                          S.abort_flag, p.status, kSiteDFull, p.wait_polls) ? 1 : 0;
                 epi_sync();
                 if (!*S.epi_ok) {
                     stop = true;
@@ -851,6 +860,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         }
                     }
                     S.P[t] = Pt;
+                    // Pt = |O c|^2 for the normalised c the rotation read (kinv carries
+                    // the deferred normalisation), so Pt - 1 is the rotation's own
+                    // relative norm error (split products, FP32 sums)
+                    nerr = fmaxf(nerr, fabsf(Pt - 1.0f));
                     const float nB = Pt - Db;
                     const float dB = Db / Pt;
                     const double lB = S.ell[t] + (double)log1pf(-dB);
@@ -984,22 +997,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
             // ---- observable partials (fixed order) -----------------------------------------
             if (e == 0) {
-                // per-CTA partials of at most TT values in [0, 1]: FP32 is exact to
-                // ~1e-6 here; the partials are summed over CTAs in FP64
-                float sx = 0.f, sx2 = 0.f;
+                // per-CTA partials in FP64 (the per-trajectory values are FP32)
+                double sx = 0.0, sx2 = 0.0;
                 for (int t = lane; t < TT; t += 32) {
                     if (S.flag[t] == 2) continue;
-                    sx += S.x[t];
-                    sx2 += S.x[t] * S.x[t];
+                    const double x = S.x[t];
+                    sx += x;
+                    sx2 += x * x;
                 }
-                sx = warp_sumf(sx);
-                sx2 = warp_sumf(sx2);
+                warp_sum2(sx, sx2);
                 if (lane == 0) {
                     p.obs_part[((size_t)blockIdx.x * K + g) * 2] = sx;
                     p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = sx2;
                 }
             }
         }
+        if (p.norm_err && etid < TT && t0 + etid < p.M) atomicMax(p.norm_err, __float_as_uint(nerr));
     }
     fence_before();
     __syncthreads();

@@ -30,20 +30,58 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_dev[kMaxDevices] = {};
+struct SavedAddress {
+    unsigned long long ctx_id = 0;  // driver id of the context the address belongs to
+    void *ptr = nullptr;
+};
+SavedAddress g_saved[kMaxDevices];
 
-// Device address of g_static_scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// Unique id of the calling thread's current CUDA context (cuCtxGetId, through
+// the runtime's driver entry points: the library does not link the driver).
+// A context created after cudaDeviceReset gets a new id even if the driver
+// reuses the old handle.
+cudaError_t current_context_id(unsigned long long *id) {
+    typedef int (*GetCurrentFn)(void **);
+    typedef int (*GetIdFn)(void *, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorSymbolNotFound;
+        get_current = reinterpret_cast<GetCurrentFn>(f0);
+        get_id = reinterpret_cast<GetIdFn>(f1);
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of g_static_scratch in the current context of `device` (the
+// device current on this thread). Looked up once per device and context, with
+// that device current, and kept; a new context on the device (after
+// cudaDeviceReset, say) makes the saved address stale, so it is looked up
+// again.
 cudaError_t scratch_address(int device, void **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_dev[device]) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    SavedAddress &s = g_saved[device];
+    if (!s.ptr || s.ctx_id != id) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_dev[device] = p;
+        s.ptr = p;
+        s.ctx_id = id;
     }
-    *out = g_scratch_dev[device];
+    *out = s.ptr;
     return cudaSuccess;
 }
 
@@ -85,6 +123,7 @@ extern "C" aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double 
     p.jcap = jump_capacity;
     p.jcount = jump_count;
     p.status = status;
+    p.norm_err = nullptr;  // the rotation-error diagnostic is not recorded here
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(jump_count, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);

@@ -204,9 +204,10 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.ehalf.assign((size_t)K * N * 2, 0.0);
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
-    const bool r64 = in.precision == AQT_PREC_FP64;
-    tab.Rt.resize(r64 ? (size_t)K * n * NN : 0);
-    tab.Rt32.resize(r64 ? 0 : (size_t)K * n * NN);
+    tab.Mdiag.assign((size_t)K * n * N, 0.0);
+    tab.gslot.assign(K, -1);
+    tab.n_general = 0;
+    tab.Rgen.clear();
     tab.lvlE.assign((size_t)K * N, 0.0);
     tab.mfirst.assign((size_t)K * N, 0);
     tab.msize.assign((size_t)K * N, 0);
@@ -373,21 +374,10 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
                     }
             }
         }
-        // jump operators with their rates absorbed (Eq. Aired): R = sqrt(gamma) M,
-        // stored source-major (Rt[b][a] = R[a][b]; M is symmetric)
-        std::vector<double> sgT(NN);  // sqrt(gamma(w_ab)) at [b][a]
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b) sgT[(size_t)b * N + a] = std::sqrt(gam[(size_t)a * N + b]);
-        for (int al = 0; al < n; ++al) {
-            const double *Ma = Mg + (size_t)al * NN;
-            const size_t base = ((size_t)g * n + al) * NN;
+        // diagonals of M_alpha (the zero-frequency jump operators, up to sqrt(gamma(0)))
+        for (int al = 0; al < n; ++al)
             for (int b = 0; b < N; ++b)
-                for (int a = 0; a < N; ++a) {
-                    const double r = sgT[(size_t)b * N + a] * Ma[(size_t)b * N + a];
-                    if (r64) tab.Rt[base + (size_t)b * N + a] = r;
-                    else tab.Rt32[base + (size_t)b * N + a] = (float)r;
-                }
-        }
+                tab.Mdiag[((size_t)g * n + al) * N + b] = Mg[(size_t)al * NN + (size_t)b * N + b];
         // half-step factors exp(-i K tau) and |.|^2
         double *eh = &tab.ehalf[(size_t)g * N * 2];
         double *dd = &tab.d2[(size_t)g * N];
@@ -400,6 +390,76 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         }
     });
     if (st != AQT_OK) return st;
+
+    // ---- pass 2b: full jump amplitudes at the grid points that need the general
+    // jump routine (Eq. Aired: R = sqrt(gamma) M, stored source-major) ----------
+    std::vector<int> general;
+    for (int g = 0; g < K; ++g)
+        if (tab.meta[g].degenerate || !tab.meta[g].simple) {
+            tab.gslot[g] = (int32_t)general.size();
+            general.push_back(g);
+        }
+    tab.n_general = (int)general.size();
+    tab.Rgen.resize((size_t)tab.n_general * n * NN);
+    parallel_for(tab.n_general, [&](int i) {
+        const int g = general[i];
+        std::vector<double> R((size_t)n * NN);
+        jump_amplitudes(in, tab, g, R.data());
+        double *dst = &tab.Rgen[(size_t)i * n * NN];
+        for (int al = 0; al < n; ++al)
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) dst[(size_t)al * NN + (size_t)b * N + a] = R[(size_t)al * NN + (size_t)a * N + b];
+    });
+
+    // ---- time-step conditions of Eq. newcond (Sec. IV; App. A, App. B.1) --------
+    // |H_eff| is the largest |K_bb| (H_eff = V K V^T with V orthogonal, K
+    // diagonal). |dH_eff/dt| is estimated from above: the schedule derivative
+    // of H_S by the triangle inequality (|H^X| = n, |H^Z| = max |E_z|), plus the
+    // rate of change of the dissipative and Lamb-shift part of the diagonal
+    // (forward differences). lambda is taken per eigenstate, lambda_b =
+    // -2 Im K_bb (the jump rate of a trajectory in level b), over the levels
+    // with a jump probability above 1e-6 over the whole run.
+    {
+        double hz_max = 0.0;
+        for (int x = 0; x < N; ++x) hz_max = std::max(hz_max, std::fabs(Ez[x]));
+        for (int i = 0; i < 3; ++i) {
+            tab.dt_bound[i] = INFINITY;
+            tab.dt_bound_at[i] = 0;
+        }
+        const double t_f = in.t_f;
+        for (int g = 0; g < K; ++g) {
+            const int g1 = g + 1 < K ? g + 1 : g - 1;  // neighbour for the difference
+            const double s0 = (double)g / (K - 1), s1 = (double)g1 / (K - 1);
+            double A0, B0, A1, B1;
+            schedule_at(in, std::min(s0, s1), &A0, &B0);
+            schedule_at(in, std::max(s0, s1), &A1, &B1);
+            const double dsdt = 1.0 / t_f, ds = std::fabs(s1 - s0);
+            const double hs_dot = (std::fabs(A1 - A0) * n + std::fabs(B1 - B0) * hz_max) / ds * dsdt;
+            const double *k0 = &tab.kdiag[(size_t)g * N * 2], *k1 = &tab.kdiag[(size_t)g1 * N * 2];
+            const double *e0 = &tab.evals[(size_t)g * N], *e1 = &tab.evals[(size_t)g1 * N];
+            const double dtg = ds * t_f;
+            double hnorm = 0.0, diss_dot = 0.0, lam_term = INFINITY;
+            for (int b = 0; b < N; ++b) {
+                hnorm = std::max(hnorm, std::hypot(k0[2 * b], k0[2 * b + 1]));
+                const double dre = (k1[2 * b] - e1[b]) - (k0[2 * b] - e0[b]);
+                const double dim = k1[2 * b + 1] - k0[2 * b + 1];
+                diss_dot = std::max(diss_dot, std::hypot(dre, dim) / dtg);
+                const double lam = -2.0 * k0[2 * b + 1], lam1 = -2.0 * k1[2 * b + 1];
+                if (!(lam * t_f > 1e-6)) continue;
+                const double lam_dot = (g1 > g ? lam1 - lam : lam - lam1) / dtg;
+                const double den = std::fabs(lam * lam - lam_dot);
+                if (den > 0.0) lam_term = std::min(lam_term, lam / den);
+            }
+            const double hdot = hs_dot + diss_dot;
+            const double terms[3] = {hdot > 0.0 ? 2.0 * hnorm / hdot : INFINITY,
+                                     hnorm > 0.0 ? 1.0 / hnorm : INFINITY, lam_term};
+            for (int i = 0; i < 3; ++i)
+                if (terms[i] < tab.dt_bound[i]) {
+                    tab.dt_bound[i] = terms[i];
+                    tab.dt_bound_at[i] = g;
+                }
+        }
+    }
 
     // ---- pass 3: frame rotations OT_g[b][a] = (V_g^T V_{g+1})[b][a] ------------
     parallel_for(K - 1, [&](int g) {
@@ -414,6 +474,18 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         gram(T0.data(), T1.data(), N, N, N, &tab.OT[(size_t)g * NN], N, false);
     });
     return AQT_OK;
+}
+
+void jump_amplitudes(const Inputs &in, const Tables &tab, int g, double *out) {
+    const int n = tab.n, N = tab.N;
+    const size_t NN = (size_t)N * N;
+    sz_frames(&tab.V[(size_t)g * NN], n, out);  // M_alpha[a][b]
+    const double *lvlE = &tab.lvlE[(size_t)g * N];
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            const double sg = std::sqrt(in.bath.gamma(lvlE[b] - lvlE[a]));
+            for (int al = 0; al < n; ++al) out[(size_t)al * NN + (size_t)a * N + b] *= sg;
+        }
 }
 
 }  // namespace aqt

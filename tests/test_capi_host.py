@@ -18,7 +18,7 @@ def _declared_symbols():
 def test_library_exports_every_declared_symbol(aqt_lib):
     lib = aqt_lib.lib()
     syms = _declared_symbols()
-    assert len(syms) >= 18
+    assert len(syms) >= 21
     for s in syms:
         assert hasattr(lib, s), s
     assert set(syms) == set(aqt_lib.EXPORTS)
@@ -30,7 +30,7 @@ def _host_ctx(A, inst, M=10, precision=0):
     A.aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
     A.aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
     A.aqt_set_grid(c, inst.t_f, inst.n_grid)
-    A.aqt_set_trajectories(c, M, 1, precision, 16)
+    A.aqt_set_trajectories(c, M, 1, precision, 0, 16)
     return c
 
 
@@ -51,9 +51,9 @@ def test_argument_validation(aqt_lib):
     with pytest.raises(A.AqtError):
         A.aqt_set_grid(c, 10.0, 1)
     with pytest.raises(A.AqtError):
-        A.aqt_set_trajectories(c, 0, 1, 0, 10)
+        A.aqt_set_trajectories(c, 0, 1, 0, 0, 10)
     with pytest.raises(A.AqtError):
-        A.aqt_set_trajectories(c, 10, 1, 7, 10)
+        A.aqt_set_trajectories(c, 10, 1, 7, 0, 10)
     with pytest.raises(A.AqtError):
         A.aqt_workspace_size(c)                                       # inputs incomplete
     with pytest.raises(A.AqtError):
@@ -141,21 +141,6 @@ def test_grid_metadata_matches_oracle(aqt_lib, n, seed, grid, idx):
     A.aqt_destroy(c)
 
 
-def test_fp32_jump_table_is_rounded_fp64(aqt_lib):
-    A = aqt_lib
-    inst = W.tfim_instance(3, 7, n_grid=5)
-    c64 = _host_ctx(A, inst, precision=0)
-    c32 = _host_ctx(A, inst, precision=1)
-    A.aqt_build_tables(c64, 0)
-    A.aqt_build_tables(c32, 0)
-    for g in (1, 4):
-        r64 = A.aqt_debug_table(c64, 3, g, (3, 8, 8))
-        r32 = A.aqt_debug_table(c32, 3, g, (3, 8, 8))
-        np.testing.assert_array_equal(r32, r64.astype(np.float32).astype(np.float64))
-    A.aqt_destroy(c64)
-    A.aqt_destroy(c32)
-
-
 def test_device_runs_limited_to_256_levels(aqt_lib):
     A = aqt_lib
     inst = W.tfim_instance(9, 3, n_grid=3)
@@ -183,3 +168,40 @@ def test_binding_fails_loudly_without_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert "raised" in r.stdout and "missing" in r.stdout
+
+
+def test_dt_condition_terms_and_warning(aqt_lib):
+    """Eq. newcond (Sec. IV): the library's three terms against the oracle's
+    generator, and AQT_WDT on a grid that is too coarse."""
+    A = aqt_lib
+    inst = W.tfim_instance(3, 7, t_f=10.0, n_grid=41)
+    c = _host_ctx(A, inst)
+    assert A.aqt_build_tables(c, 0) == A.AQT_OK
+    b, at = A.aqt_get_dt_bounds(c)
+    s = np.arange(inst.n_grid) / (inst.n_grid - 1)
+    dt = inst.t_f / (inst.n_grid - 1)
+    frames = [lindblad.Frame(inst, float(x)) for x in s]
+    heff = [f.eig.V @ f.K @ f.eig.V.T for f in frames]
+    hn = np.array([np.linalg.norm(h, 2) for h in heff])
+    # 1/|H_eff| is exact: the operator norm of the oracle's H_eff
+    assert b[1] == pytest.approx(1.0 / hn.max(), rel=1e-9)
+    assert at[1] == int(np.argmax(hn))
+    # 2|H_eff|/|dH_eff/dt| uses an upper estimate of the derivative: never above the
+    # value with the exact finite-difference derivative, and not far below it
+    hdot = np.array([np.linalg.norm(heff[g + 1] - heff[g], 2) / dt for g in range(inst.n_grid - 1)])
+    fd = np.min(2 * hn[:-1] / hdot)
+    assert b[0] <= fd * (1 + 1e-6) and b[0] > 0.2 * fd
+    # lambda term per eigenstate: lambda_b = -2 Im K_bb
+    lam = np.array([-2 * np.diag(f.K).imag for f in frames])
+    ref = np.inf
+    for g in range(inst.n_grid - 1):
+        ld = (lam[g + 1] - lam[g]) / dt
+        ok = lam[g] * inst.t_f > 1e-6
+        ref = min(ref, np.min(np.abs(lam[g][ok] / (lam[g][ok] ** 2 - ld[ok]))))
+    assert b[2] <= ref * (1 + 1e-6)
+    A.aqt_destroy(c)
+    coarse = W.tfim_instance(3, 7, t_f=10.0, n_grid=3)
+    c = _host_ctx(A, coarse)
+    assert A.aqt_build_tables(c, 0) == A.AQT_WDT
+    assert "newcond" in A.aqt_last_error(c)
+    A.aqt_destroy(c)

@@ -17,16 +17,18 @@ from oracle import ame, trajectories
 pytestmark = pytest.mark.gpu
 
 
-def run_lib(A, inst, precision, M=None, jcap=None):
-    S = A.Session(inst, precision=precision, M=M, jump_capacity=jcap)
+def run_lib(A, inst, precision, M=None, jcap=None, timing=0):
+    S = A.Session(inst, precision=precision, M=M, jump_capacity=jcap, timing=timing)
     S.build()
     status = S.run()
     mean, se = S.observables()
     s1, s2 = A.aqt_get_observable_sums(S.ctx, inst.n_grid)
     jumps, dropped = S.jumps()
     final = S.final_state(basis=1)
+    roterr = A.aqt_get_rotation_error(S.ctx)
     S.close()
-    return dict(status=status, mean=mean, se=se, s1=s1, s2=s2, jumps=jumps, dropped=dropped, final=final)
+    return dict(status=status, mean=mean, se=se, s1=s1, s2=s2, jumps=jumps, dropped=dropped, final=final,
+                roterr=roterr)
 
 
 def se_bound(ref, M):
@@ -43,9 +45,9 @@ def jumps_by_traj(recs):
     return out
 
 
-def compare_crn(inst, res, traj_ids, t_tol, state_tol, min_identical=1.0):
+def compare_crn(inst, res, traj_ids, t_tol, state_tol, min_identical=1.0, timing="refined"):
     """Oracle on traj_ids with the same streams; returns the oracle output."""
-    p, ojumps, ofin = trajectories.sample(inst, traj_ids)
+    p, ojumps, ofin = trajectories.sample(inst, traj_ids, timing=timing)
     gj = jumps_by_traj(res["jumps"])
     oj = jumps_by_traj(ojumps)
     identical = 0
@@ -150,3 +152,26 @@ def test_minimal_sizes(aqt_lib):
     res = run_lib(A, inst, A.AQT_PREC_FP64, M=1)
     p, oj, _ = compare_crn(inst, res, [0], t_tol=1e-12, state_tol=1e-12)
     np.testing.assert_allclose(res["s1"], p.sum(axis=0), atol=1e-12)
+
+
+def test_grid_timing_fp64_every_trajectory(aqt_lib):
+    """GRID jump timing (jump at the end of the frozen half-step in which the
+    norm fell to the threshold) against the oracle's GRID sampler."""
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=5.0, n_grid=101, seed=99)
+    M = 37
+    res = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_FP64, M=M, timing=aqt_lib.AQT_JUMP_GRID)
+    assert res["status"] == aqt_lib.AQT_OK
+    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-12, state_tol=1e-10, timing="grid")
+    assert len(oj) > 10 and len(res["jumps"]) == len(oj)
+    np.testing.assert_allclose(res["s1"], p.sum(axis=0), rtol=0, atol=1e-9)
+
+
+def test_rotation_norm_error_fp64_fp32(aqt_lib):
+    """P12 on the kernels' own arithmetic: the largest relative change of the
+    squared norm over one frame rotation (1e-5 budget for FP32)."""
+    inst = W.tfim_instance(6, 46, eta_g2=0.02, t_f=6.0, n_grid=201, seed=4)
+    r64 = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_FP64, M=64)
+    r32 = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_FP32, M=64)
+    assert 0.0 < r64["roterr"] < 1e-12
+    assert 0.0 < r32["roterr"] < 1e-5
+

@@ -68,8 +68,76 @@ def test_tc_rejects_small_n(aqt_lib):
     A.aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
     A.aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
     A.aqt_set_grid(c, inst.t_f, inst.n_grid)
-    A.aqt_set_trajectories(c, 10, 1, A.AQT_PREC_F16SPLIT, 16)
+    A.aqt_set_trajectories(c, 10, 1, A.AQT_PREC_F16SPLIT, 0, 16)
     with pytest.raises(A.AqtError) as e:
         A.aqt_workspace_size(c)
     assert e.value.status == A.AQT_EINVAL
     A.aqt_destroy(c)
+
+
+def test_tc_general_jumps_at_degenerate_start(aqt_lib):
+    """Jumps while the generator is frozen at s = 0, where H_S(0) has degenerate
+    manifolds: the tensor-core kernel resolves them with the general FP64 jump
+    routine. Against the FP64 GPU path (same streams) and the oracle."""
+    A = aqt_lib
+    inst = W.tfim_instance(7, 31, eta_g2=0.05, beta=0.15, t_f=2.0, n_grid=9, seed=5)
+    M = 96
+    r64 = run_lib(A, inst, A.AQT_PREC_FP64, M=M)
+    rtc = run_lib(A, inst, A.AQT_PREC_F16SPLIT, M=M)
+    assert rtc["status"] == A.AQT_OK and r64["status"] == A.AQT_OK
+    at0 = rtc["jumps"][rtc["jumps"]["grid"] == 0]
+    assert len(at0) >= 5
+    j64, jtc = {}, {}
+    for src, dst in ((r64, j64), (rtc, jtc)):
+        for r in src["jumps"]:
+            dst.setdefault(int(r["traj"]), []).append((r["grid"], r["half"], r["alpha"], r["src"], r["dst"]))
+    same = [t for t in range(M) if j64.get(t, []) == jtc.get(t, [])]
+    assert len(same) >= 0.9 * M
+    ov = np.abs(np.einsum("mi,mi->m", r64["final"][same].conj(), rtc["final"][same]))
+    assert np.max(np.abs(ov - 1.0)) < 2e-5
+    compare_crn(inst, rtc, list(range(12)), t_tol=1e-5, state_tol=2e-5, min_identical=0.8)
+
+
+def test_tc_wait_timeout_reports_and_recovers(aqt_lib):
+    """A bounded wait made to expire (poll limit 0): the run ends with
+    AQT_ETIMEOUT naming the wait, having issued no products; the same context
+    then runs normally and reproduces a fresh context's result."""
+    A = aqt_lib
+    inst = W.tfim_instance(7, 207, eta_g2=0.02, t_f=8.0, n_grid=41, seed=5)
+    S = A.Session(inst, precision=A.AQT_PREC_F16SPLIT, M=64)
+    S.build()
+    A.aqt_set_wait_limit(S.ctx, 0)
+    A.aqt_run(S.ctx, S.stream())
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_sync(S.ctx)
+    assert e.value.status == A.AQT_ETIMEOUT and "B operand ready" in str(e.value)
+    A.aqt_set_wait_limit(S.ctx, 1 << 22)
+    assert S.run() == A.AQT_OK
+    s1, s2 = A.aqt_get_observable_sums(S.ctx, inst.n_grid)
+    fin = S.final_state(basis=0)
+    S.close()
+    T = A.Session(inst, precision=A.AQT_PREC_F16SPLIT, M=64)
+    T.build()
+    assert T.run() == A.AQT_OK
+    t1, t2 = A.aqt_get_observable_sums(T.ctx, inst.n_grid)
+    assert np.array_equal(s1, t1) and np.array_equal(s2, t2)
+    assert np.array_equal(fin, T.final_state(basis=0))
+    T.close()
+
+
+def test_tc_grid_timing_matches_fp64(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(7, 207, eta_g2=0.02, t_f=8.0, n_grid=301, seed=5)
+    M = 200
+    r64 = run_lib(A, inst, A.AQT_PREC_FP64, M=M, timing=A.AQT_JUMP_GRID)
+    rtc = run_lib(A, inst, A.AQT_PREC_F16SPLIT, M=M, timing=A.AQT_JUMP_GRID)
+    assert rtc["status"] == A.AQT_OK
+    tau = 0.5 * inst.t_f / (inst.n_grid - 1)
+    assert np.all(np.abs(rtc["jumps"]["t"] / tau - np.round(rtc["jumps"]["t"] / tau)) < 1e-6)
+    j64, jtc = {}, {}
+    for src, dst in ((r64, j64), (rtc, jtc)):
+        for r in src["jumps"]:
+            dst.setdefault(int(r["traj"]), []).append((r["grid"], r["half"], r["alpha"], r["src"], r["dst"]))
+    same = [t for t in range(M) if j64.get(t, []) == jtc.get(t, [])]
+    assert len(same) >= 0.95 * M
+

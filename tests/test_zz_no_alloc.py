@@ -15,13 +15,15 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_static_scratch_matches_ordinary_run(aqt_lib):
+@pytest.mark.parametrize("n,M,grid,precision", [(3, 300, 201, 0), (7, 64, 101, 2)])
+def test_static_scratch_matches_ordinary_run(aqt_lib, n, M, grid, precision):
+    """FP64 SIMT path (jump vectors in the static array) and tensor-core path
+    (jump vectors and per-trajectory patch products in the static array)."""
     import torch
 
     A = aqt_lib
-    inst = W.tfim_instance(3, 44, eta_g2=0.02, t_f=6.0, n_grid=201, seed=3)
-    M = 300
-    S = A.Session(inst, precision=A.AQT_PREC_FP64, M=M)
+    inst = W.tfim_instance(n, 44 + n, eta_g2=0.02, t_f=6.0, n_grid=grid, seed=3)
+    S = A.Session(inst, precision=precision, M=M)
     S.build()
     assert S.run() == A.AQT_OK
     ref_s1, ref_s2 = A.aqt_get_observable_sums(S.ctx, inst.n_grid)
@@ -46,15 +48,15 @@ def test_static_scratch_matches_ordinary_run(aqt_lib):
         n = int(cnt.item())
         assert n == len(ref_jumps), (call, n, len(ref_jumps))
         o = obs.cpu().numpy()
-        np.testing.assert_allclose(o[:, 0], ref_s1, rtol=0, atol=1e-12)
-        np.testing.assert_allclose(o[:, 1], ref_s2, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(o[:, 0], ref_s1)
+        np.testing.assert_array_equal(o[:, 1], ref_s2)
         f = fin.cpu().numpy()
-        np.testing.assert_allclose(f[..., 0] + 1j * f[..., 1], ref_final, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(f[..., 0] + 1j * f[..., 1], ref_final)
         recs = np.frombuffer(jrec.cpu().numpy().tobytes()[: n * A.JUMP_DTYPE.itemsize], dtype=A.JUMP_DTYPE)
         got = sorted((int(r["traj"]), float(r["t"]), int(r["src"]), int(r["dst"])) for r in recs)
         exp = sorted((int(r["traj"]), float(r["t"]), int(r["src"]), int(r["dst"])) for r in ref_jumps)
         assert [g[0::2] + (g[3],) for g in got] == [e[0::2] + (e[3],) for e in exp]
-        assert max(abs(g[1] - e[1]) for g, e in zip(got, exp)) < 1e-12
+        assert all(g[1] == e[1] for g, e in zip(got, exp))
     S.close()
 
 
@@ -66,7 +68,7 @@ def test_static_scratch_rejects_oversized_runs(aqt_lib):
     A.aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
     A.aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
     A.aqt_set_grid(c, inst.t_f, inst.n_grid)
-    A.aqt_set_trajectories(c, 200_000, 1, A.AQT_PREC_FP64, 16)
+    A.aqt_set_trajectories(c, 200_000, 1, A.AQT_PREC_FP64, 0, 16)
     with pytest.raises(A.AqtError) as e:
         A.aqt_run_static_scratch(c, 0, 1 << 20, 1 << 20, 1 << 20, 16, 1 << 20, 1 << 20)
     assert e.value.status == A.AQT_EINVAL and "static array" in str(e.value)
