@@ -11,6 +11,8 @@ Stream layout (a reading: the paper only says "draw a random number", Sec. IV):
   event j >= 1     -> x0: u1 (source draw), x1: u2 (target draw),
                       x2: threshold r after the j-th jump
   uniform(x)       = ((x >> 12) + 0.5) * 2**-52, strictly inside (0, 1)
+Fixed-step sampler (App. B.1), one block per frozen piece q of the grid:
+  counter = (trajectory index, q, 1, 0) -> x0: eps (jump test), x1: u1, x2: u2
                      (every value is a multiple of 2**-53, so exact in FP64)
 """
 from __future__ import annotations
@@ -55,3 +57,10 @@ def jump_draws(seed: int, traj: int, j: int):
     """(u1, u2, r_next) for the j-th jump (j >= 1) of a trajectory."""
     x = event_block(seed, traj, j)
     return uniform(x[0]), uniform(x[1]), uniform(x[2])
+
+
+def fixed_step_draws(seed: int, traj: int, piece: int):
+    """(eps, u1, u2) of the fixed-step sampler for frozen piece ``piece``."""
+    x = philox4x64((traj, piece, 1, 0), (seed, KEY_HI))
+    return uniform(x[0]), uniform(x[1]), uniform(x[2])
+

@@ -173,3 +173,53 @@ def sample(inst, traj_ids, seed=None, timing: str = "refined"):
     jumps = [j for tr in trajs for j in tr.jumps]
     final = np.array([tr.psi / np.linalg.norm(tr.psi) for tr in trajs])
     return p, jumps, final
+
+
+def sample_fixed_step(inst, traj_ids, seed=None):
+    """The fixed-step unravelling of App. B.1 on the same frozen pieces.
+
+    At the start of each piece (length tau, generator frozen) with normalised
+    psi: lambda = sum_i <A_i^dag A_i> = -2 Im <psi|H_eff|psi> (Eq. lambda),
+    Delta p = tau lambda, and with a fresh uniform eps a jump happens when
+    Delta p > eps; its channel is drawn with the probabilities Pi_i (Eq.
+    Pi(t)), and the jump replaces the piece's deterministic evolution. Without
+    a jump psi <- exp(-i H_eff tau) psi, renormalised. Piece q (q = 0, 1, ...
+    in time order) draws from ``philox.fixed_step_draws(seed, traj, q)``.
+    Returns the same triple as ``sample``; jump times are the pieces' starts.
+    """
+    seed = inst.seed if seed is None else seed
+    s_grid, dt = model.grid(inst)
+    tau = 0.5 * dt
+    K = len(s_grid)
+    p = np.empty((len(traj_ids), K))
+    psis, jumps, prev = None, [], None
+
+    def step(piece, psi, traj, q, t0, g, half):
+        lam = -2.0 * np.vdot(psi, piece.Heff @ psi).imag
+        eps, u1, u2 = philox.fixed_step_draws(seed, traj, q)
+        if tau * lam > eps:
+            al, m, a, cls, new = choose_jump(piece.fr, psi, u1, u2)
+            eig = piece.fr.eig
+            jumps.append(dict(traj=traj, grid=g, half=half, t=t0, alpha=al, src=int(eig.manifolds[m][0]),
+                              dst=int(eig.manifolds[eig.level_manifold[a]][0]),
+                              omega=float(eig.E[m] - eig.E[eig.level_manifold[a]])))
+            return new
+        v = piece.U_tau @ psi
+        return v / np.linalg.norm(v)
+
+    for k, fr in enumerate(ame.frames(inst)):
+        piece = Piece(fr, tau)
+        if k == 0:
+            psis = [fr.eig.V[:, 0].astype(complex) for _ in traj_ids]
+        else:
+            t_prev = (k - 1) * dt
+            for i, tr in enumerate(traj_ids):
+                psis[i] = step(prev, psis[i], int(tr), 2 * k - 2, t_prev, k - 1, 1)
+                psis[i] = step(piece, psis[i], int(tr), 2 * k - 1, t_prev + tau, k, 0)
+        g0 = fr.eig.manifolds[0]
+        for i in range(len(traj_ids)):
+            c = fr.eig.V[:, g0].T @ psis[i]
+            p[i, k] = float(np.sum(np.abs(c) ** 2))
+        prev = piece
+    return p, jumps, np.array(psis)
+

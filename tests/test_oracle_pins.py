@@ -506,3 +506,48 @@ def test_grid_timing_jumps_at_the_end_of_the_refined_piece():
         assert abs(b["t"] - end) < 1e-12
     for j in jg:   # every GRID jump sits on a piece boundary
         assert abs(j["t"] / tau - round(j["t"] / tau)) < 1e-9
+
+
+# --- Fixed-step unravelling (App. B.1) ---------------------------------------------------------
+def test_fixed_step_first_jump_is_geometric():
+    """App. B.1: in each time step a jump happens with probability
+    Delta p = dt lambda. From an eigenstate at frozen s (lambda constant until
+    the first jump) the step of the first jump is geometric with parameter
+    tau lambda, lambda = -2 Im K_bb."""
+    inst = W.tfim_instance(1, 27, eta_g2=0.08, t_f=40.0, n_grid=41, lamb_shift=False)
+    f = _frozen(inst, 0.5)
+    inst.sched_s, inst.sched_A, inst.sched_B = f["sched_s"], f["sched_A"], f["sched_B"]
+    fr = lindblad.Frame(inst, 0.5)
+    tau = 0.5 * inst.t_f / (inst.n_grid - 1)
+    pj = tau * (-2 * fr.K[0, 0].imag)
+    M = 3000
+    _, jumps, _ = trajectories.sample_fixed_step(inst, range(M))
+    first = {}
+    for j in jumps:
+        if j["traj"] not in first:
+            first[j["traj"]] = int(round(j["t"] / tau))    # piece index of the first jump
+    npieces = 2 * (inst.n_grid - 1)
+    counts = np.bincount(list(first.values()), minlength=npieces)[:npieces]
+    # pool the pieces into 8 bins of equal width against the geometric law
+    edges = np.linspace(0, npieces, 9).astype(int)
+    obs = [counts[a:b].sum() for a, b in zip(edges[:-1], edges[1:])] + [M - len(first)]
+    q = np.arange(npieces)
+    pq = (1 - pj) ** q * pj
+    exp = [M * pq[a:b].sum() for a, b in zip(edges[:-1], edges[1:])] + [M * (1 - pj) ** npieces]
+    chi2 = float(np.sum((np.array(obs) - np.array(exp)) ** 2 / np.array(exp)))
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3, (obs, exp)
+
+
+def test_fixed_step_average_matches_density_matrix():
+    """The fixed-step unravelling averages to the AME up to its O(dt) bias
+    (App. B.1); with tau lambda ~ 1e-3 the bias is far below the statistical
+    error at M = 1500 (3.5 sigma, sigma >= sqrt(p (1 - p) / M))."""
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=5.0, n_grid=201, seed=99)
+    ref = ame.run(inst)["p_gs"]
+    M = 1500
+    p, jumps, _ = trajectories.sample_fixed_step(inst, range(M))
+    assert len(jumps) > 500
+    for k in (40, 80, 120, 160, 200):
+        mean = p[:, k].mean()
+        se = max(p[:, k].std(ddof=1) / math.sqrt(M), math.sqrt(ref[k] * (1 - ref[k]) / M))
+        assert abs(mean - ref[k]) < 3.5 * se, (k, mean, ref[k], se)
