@@ -81,8 +81,14 @@ typedef enum {
  * condition, not how finely tau is resolved. */
 typedef enum {
     AQT_JUMP_REFINED = 0,   /* at the root of |psi(t)|^2 = r inside the half-step (FP64 Newton) */
-    AQT_JUMP_GRID = 1       /* at the end of the half-step in which |psi|^2 fell to r: the
+    AQT_JUMP_GRID = 1,      /* at the end of the half-step in which |psi|^2 fell to r: the
                                time-step-resolution variant, with an O(dt) bias in the jump times */
+    AQT_JUMP_FIXED_STEP = 2 /* the fixed-step unravelling of App. B.1: at the start of each half-step
+                               (length tau) a jump happens with probability tau lambda, lambda =
+                               sum_i <A_i^dag A_i> (Eq. lambda), its channel drawn by Eq. Pi(t), in
+                               place of that half-step's no-jump evolution; O(dt) bias. Draws:
+                               counter (trajectory, half-step index, 1, 0) -> (jump test, u1, u2).
+                               SIMT paths only (AQT_PREC_FP64, AQT_PREC_FP32) */
 } aqt_jump_timing;
 
 /* One jump. t is the jump time in ns; the jump happened while the generator
@@ -166,9 +172,9 @@ aqt_status aqt_build_tables(aqt_ctx *ctx, void *stream);
  * Lamb-shift diagonal), so the first term is a lower estimate; lambda is taken
  * per instantaneous eigenstate (lambda_b = -2 Im K_bb, levels whose jump
  * probability over the run exceeds 1e-6). aqt_build_tables returns AQT_WDT
- * when dt > 0.1 x the first term, or, with AQT_JUMP_GRID, the third; the
- * second bounds a first-order no-jump step and does not apply to the exact
- * frozen-generator phases used here. Needs the host tables (aqt_build_tables
+ * when dt > 0.1 x the first term, or, with AQT_JUMP_GRID or
+ * AQT_JUMP_FIXED_STEP, the third; the second bounds a first-order no-jump step
+ * and does not apply to the exact frozen-generator phases used here. Needs the host tables (aqt_build_tables
  * or aqt_workspace_size). */
 aqt_status aqt_get_dt_bounds(aqt_ctx *ctx, double *bounds, int32_t *at);
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libaqt.so")
 AQT_OK, AQT_EINVAL, AQT_ECUDA, AQT_ENOMEM, AQT_EOVERFLOW, AQT_ENUMERIC, AQT_ENOCONV, AQT_EDEGEN, AQT_ENODEV, AQT_ETIMEOUT, \
     AQT_WDT = range(11)
 AQT_PREC_FP64, AQT_PREC_FP32, AQT_PREC_F16SPLIT = 0, 1, 2
-AQT_JUMP_REFINED, AQT_JUMP_GRID = 0, 1
+AQT_JUMP_REFINED, AQT_JUMP_GRID, AQT_JUMP_FIXED_STEP = 0, 1, 2
 STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4: "AQT_EOVERFLOW",
                 5: "AQT_ENUMERIC", 6: "AQT_ENOCONV", 7: "AQT_EDEGEN", 8: "AQT_ENODEV", 9: "AQT_ETIMEOUT",
                 10: "AQT_WDT"}

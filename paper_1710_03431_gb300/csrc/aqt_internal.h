@@ -135,8 +135,10 @@ struct DevTables {
 
 // When a jump happens inside a frozen half-step (Sec. IV): at the root of the
 // norm-crossing condition (REFINED), or at the end of the half-step in which
-// the norm fell to the threshold (GRID).
-enum JumpTiming : int { kTimingRefined = 0, kTimingGrid = 1 };
+// the norm fell to the threshold (GRID); or the fixed-step sampler of App. B.1
+// (FIXED: a jump test with probability tau lambda at the start of each
+// half-step).
+enum JumpTiming : int { kTimingRefined = 0, kTimingGrid = 1, kTimingFixed = 2 };
 
 struct RunParams {
     int n, N, K, TT, RA, n_cta;

@@ -130,6 +130,8 @@ aqt_status device_shape_check(aqt_ctx *c) {
     if (c->in.n > 8) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 8 (N <= 256)");
     if (c->in.precision == AQT_PREC_F16SPLIT && c->in.n < 7)
         return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
+    if (c->in.precision == AQT_PREC_F16SPLIT && c->in.timing == AQT_JUMP_FIXED_STEP)
+        return fail(c, AQT_EINVAL, "the fixed-step sampler runs on the SIMT paths (AQT_PREC_FP64, AQT_PREC_FP32)");
     return AQT_OK;
 }
 
@@ -203,13 +205,13 @@ aqt_status ensure_host_tables(aqt_ctx *c) {
 // dt <= 0.1 x the term. The 1/|H_eff| term bounds the error of a first-order
 // no-jump step; here the frozen-generator phases are exact, so it is reported
 // (aqt_get_dt_bounds) but not checked. The lambda term bounds the error of a
-// fixed-step jump probability, which only GRID timing makes.
+// fixed-step jump probability, which GRID timing and the fixed-step sampler make.
 aqt_status dt_warning(aqt_ctx *c) {
     const Tables &t = c->tab;
     static const char *what[3] = {"2|H_eff|/|dH_eff/dt|", "1/|H_eff|", "|lambda/(lambda^2 - dlambda/dt)|"};
     std::string msg;
     for (int i = 0; i < 3; ++i) {
-        if (i == 1 || (i == 2 && c->in.timing != AQT_JUMP_GRID)) continue;
+        if (i == 1 || (i == 2 && c->in.timing == AQT_JUMP_REFINED)) continue;
         if (t.dt > 0.1 * t.dt_bound[i])
             msg += std::string(msg.empty() ? "" : "; ") + "dt = " + std::to_string(t.dt) + " ns is not << " + what[i] +
                    " = " + std::to_string(t.dt_bound[i]) + " ns (grid point " + std::to_string(t.dt_bound_at[i]) + ")";
@@ -348,7 +350,7 @@ aqt_status aqt_set_trajectories(aqt_ctx *c, int64_t M, uint64_t seed, int precis
     if (M < 1 || M > (int64_t)1 << 31) return fail(c, AQT_EINVAL, "M must be in [1, 2^31]");
     if (precision != AQT_PREC_FP64 && precision != AQT_PREC_FP32 && precision != AQT_PREC_F16SPLIT)
         return fail(c, AQT_EINVAL, "unknown precision");
-    if (jump_timing != AQT_JUMP_REFINED && jump_timing != AQT_JUMP_GRID)
+    if (jump_timing != AQT_JUMP_REFINED && jump_timing != AQT_JUMP_GRID && jump_timing != AQT_JUMP_FIXED_STEP)
         return fail(c, AQT_EINVAL, "unknown jump timing");
     if (jump_capacity < 0) return fail(c, AQT_EINVAL, "jump_capacity must be >= 0");
     c->in.M = M;

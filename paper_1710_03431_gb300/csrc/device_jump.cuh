@@ -346,6 +346,171 @@ static __device__ __forceinline__ void m_column(const RunParams &p, int g, int a
     for (int j = 0; j < NPL; ++j) m[j] = (32 * j + lane == b ? T(1) : T(0)) - T(2) * m[j];
 }
 
+// Draw the jump channel with (u1, u2) (two stages, App. B.1 Eq. Pi(t)) and
+// apply its Bohr-class operator (Eq. jump) to the normalised state held in
+// registers (level a = 32 j + lane), which is replaced by the normalised
+// post-jump state. Returns alpha, or -1 on a numeric failure; *bsrc_out and
+// *adst_out get the source and target levels.
+template <typename T, int NPL>
+static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&cr)[NPL], T (&ci)[NPL], double u1,
+                                                 double u2, int lane, double2 *slow, int *bsrc_out, int *adst_out) {
+    const int N = p.N, n = p.n;
+    const GridMeta meta = p.tab.meta[g];
+    const double *kd = p.tab.kdiag + (size_t)g * N * 2;
+    const double *Gg = p.tab.G + (size_t)g * n * N;
+    const bool fast = meta.simple && !meta.degenerate;
+    auto kim2d = [&](int j) -> double {
+        const int a = 32 * j + lane;
+        return a < N ? 2.0 * kd[2 * a + 1] : 0.0;
+    };
+    auto pop = [&](int j) -> double { return (double)cr[j] * (double)cr[j] + (double)ci[j] * (double)ci[j]; };
+    int al = -1, bsrc = -1, adst = -1;
+    if (fast) {
+        double qv[NPL];
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) qv[j] = pop(j);
+        // stage one over units (alpha, b) in that order. The total rate is
+        // sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2 2 Im K_bb, so the
+        // walk over alpha stops at the first alpha whose cumulative sum passes
+        // the target, one warp sum per alpha visited.
+        double total = 0.0, cum = 0.0, cum_last = 0.0;
+        int last = -1;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2d(j);
+        total = warp_sum(total);
+        const double target = u1 * total;
+        for (int a_ = 0; a_ < n && al < 0; ++a_) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                const int b = 32 * j + lane;
+                if (b < N) acc += qv[j] * Gg[(size_t)a_ * N + b];
+            }
+            acc = warp_sum(acc);
+            if (acc > 0.0) {
+                last = a_;
+                cum_last = cum;
+            }
+            if (acc > 0.0 && cum + acc > target) al = a_;
+            else cum += acc;
+        }
+        if (al < 0) {  // rounding at the top of the distribution
+            al = last;
+            cum = cum_last;
+        }
+        if (al >= 0) {
+            double w[NPL];
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                const int b = 32 * j + lane;
+                w[j] = b < N ? qv[j] * Gg[(size_t)al * N + b] : 0.0;
+            }
+            bsrc = reg_pick(w, target - cum, lane);
+        }
+        if (bsrc >= 0) {
+            // stage two: target a with weight gamma(E_b - E_a) M_alpha[a][b]^2
+            T m[NPL];
+            m_column<T, NPL>(p, g, al, bsrc, lane, m);
+            const double *lvlE = p.tab.lvlE + (size_t)g * N;
+            const double eb = lvlE[bsrc];
+            double w[NPL], tot2 = 0.0;
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                const int a = 32 * j + lane;
+                w[j] = a < N ? bath_gamma(p, eb - lvlE[a]) * ((double)m[j] * (double)m[j]) : 0.0;
+                tot2 += w[j];
+            }
+            tot2 = warp_sum(tot2);
+            adst = reg_pick(w, u2 * tot2, lane);
+            if (adst >= 0 && adst != bsrc) {
+                // nonzero frequency: the class is the single pair (adst <- bsrc), so
+                // the normalised result is sign(M[adst][bsrc]) c_bsrc / |c_bsrc| on adst
+                const T br = __shfl_sync(0xffffffffu, reg_at(cr, bsrc >> 5), bsrc & 31);
+                const T bi = __shfl_sync(0xffffffffu, reg_at(ci, bsrc >> 5), bsrc & 31);
+                const T ra = __shfl_sync(0xffffffffu, reg_at(m, adst >> 5), adst & 31);
+                const T m2 = br * br + bi * bi;
+                if (m2 > T(0)) {
+                    const T f = (ra < T(0) ? T(-1) : T(1)) * m_rsqrt(m2);
+#pragma unroll
+                    for (int j = 0; j < NPL; ++j) {
+                        const bool hit = 32 * j + lane == adst;
+                        cr[j] = hit ? br * f : T(0);
+                        ci[j] = hit ? bi * f : T(0);
+                    }
+                } else {
+                    al = -1;
+                }
+            } else if (adst >= 0) {
+                // zero frequency: every level pairs with itself, y_a = sqrt(gamma(0)) M_alpha[a][a] c_a
+                const double *Md = p.tab.Mdiag + ((size_t)g * n + al) * N;
+                T s = T(0);
+#pragma unroll
+                for (int j = 0; j < NPL; ++j) {
+                    const int a = 32 * j + lane;
+                    const T d = a < N ? (T)Md[a] : T(0);
+                    cr[j] *= d;
+                    ci[j] *= d;
+                    s += cr[j] * cr[j] + ci[j] * ci[j];
+                }
+                s = warp_sum(s);
+                if (s > T(0)) {
+                    const T inv = m_rsqrt(s);
+#pragma unroll
+                    for (int j = 0; j < NPL; ++j) {
+                        cr[j] *= inv;
+                        ci[j] *= inv;
+                    }
+                } else {
+                    al = -1;
+                }
+            }
+        }
+        if (bsrc < 0 || adst < 0) al = -1;
+    } else {
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const int a = 32 * j + lane;
+            if (a < N) slow[a] = make_double2((double)cr[j], (double)ci[j]);
+        }
+        __syncwarp();
+        al = general_draw_apply(p, g, u1, u2, slow, slow + N, lane, &bsrc, &adst);
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const int a = 32 * j + lane;
+            if (a < N) {
+                cr[j] = (T)slow[a].x;
+                ci[j] = (T)slow[a].y;
+            }
+        }
+        __syncwarp();
+    }
+    *bsrc_out = bsrc;
+    *adst_out = adst;
+    return al;
+}
+
+// Append one jump record (lane 0; records past the capacity are counted, not kept).
+static __device__ __forceinline__ void record_jump(const RunParams &p, int64_t traj, int g, int half, int al, int bsrc,
+                                                   int adst, double t, int lane) {
+    const int N = p.N;
+    if (lane == 0) {
+        const unsigned long long idx = atomicAdd(p.jcount, 1ull);
+        if ((int64_t)idx < p.jcap) {
+            const double *lvlE = p.tab.lvlE + (size_t)g * N;
+            aqt_jump rec;
+            rec.traj = (int32_t)traj;
+            rec.grid = g;
+            rec.half = half;
+            rec.alpha = al;
+            rec.src = bsrc;
+            rec.dst = p.tab.mfirst[(size_t)g * N + adst];
+            rec.t = t;
+            rec.omega = lvlE[bsrc] - lvlE[adst];
+            p.jumps[idx] = rec;
+        }
+    }
+}
+
 // One frozen half-step of one trajectory that may cross its threshold,
 // resolved by one warp with the state in registers (NPL levels per lane,
 // 32 NPL >= N). sre/sim: the state, level a at [a * stride] (normalised or
@@ -359,11 +524,8 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
                                                       T *sim, int stride, double &ell, double &logr, int &nj,
                                                       int lane, double2 *slow, const float2 *klev = nullptr) {
     constexpr bool f32 = std::is_same<T, float>::value;
-    const int N = p.N, n = p.n;
-    const GridMeta meta = p.tab.meta[g];
+    const int N = p.N;
     const double *kd = p.tab.kdiag + (size_t)g * N * 2;
-    const double *Gg = p.tab.G + (size_t)g * n * N;
-    const bool fast = meta.simple && !meta.degenerate;
     T cr[NPL], ci[NPL];
 #pragma unroll
     for (int j = 0; j < NPL; ++j) {
@@ -506,146 +668,13 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         ++nj;
         const Philox4 rnd = traj_event(p.seed, traj, nj);
         const double u1 = uniform01(rnd.x[0]), u2 = uniform01(rnd.x[1]), u3 = uniform01(rnd.x[2]);
-        int al = -1, bsrc = -1, adst = -1;
-        if (fast) {
-            double qv[NPL];
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) qv[j] = pop(j);
-            // stage one over units (alpha, b) in that order. The total rate is
-            // sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2 2 Im K_bb, so the
-            // walk over alpha stops at the first alpha whose cumulative sum passes
-            // the target, one warp sum per alpha visited.
-            double total = 0.0, cum = 0.0, cum_last = 0.0;
-            int last = -1;
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2d(j);
-            total = warp_sum(total);
-            const double target = u1 * total;
-            for (int a_ = 0; a_ < n && al < 0; ++a_) {
-                double acc = 0.0;
-#pragma unroll
-                for (int j = 0; j < NPL; ++j) {
-                    const int b = 32 * j + lane;
-                    if (b < N) acc += qv[j] * Gg[(size_t)a_ * N + b];
-                }
-                acc = warp_sum(acc);
-                if (acc > 0.0) {
-                    last = a_;
-                    cum_last = cum;
-                }
-                if (acc > 0.0 && cum + acc > target) al = a_;
-                else cum += acc;
-            }
-            if (al < 0) {  // rounding at the top of the distribution
-                al = last;
-                cum = cum_last;
-            }
-            if (al >= 0) {
-                double w[NPL];
-#pragma unroll
-                for (int j = 0; j < NPL; ++j) {
-                    const int b = 32 * j + lane;
-                    w[j] = b < N ? qv[j] * Gg[(size_t)al * N + b] : 0.0;
-                }
-                bsrc = reg_pick(w, target - cum, lane);
-            }
-            if (bsrc >= 0) {
-                // stage two: target a with weight gamma(E_b - E_a) M_alpha[a][b]^2
-                T m[NPL];
-                m_column<T, NPL>(p, g, al, bsrc, lane, m);
-                const double *lvlE = p.tab.lvlE + (size_t)g * N;
-                const double eb = lvlE[bsrc];
-                double w[NPL], tot2 = 0.0;
-#pragma unroll
-                for (int j = 0; j < NPL; ++j) {
-                    const int a = 32 * j + lane;
-                    w[j] = a < N ? bath_gamma(p, eb - lvlE[a]) * ((double)m[j] * (double)m[j]) : 0.0;
-                    tot2 += w[j];
-                }
-                tot2 = warp_sum(tot2);
-                adst = reg_pick(w, u2 * tot2, lane);
-                if (adst >= 0 && adst != bsrc) {
-                    // nonzero frequency: the class is the single pair (adst <- bsrc), so
-                    // the normalised result is sign(M[adst][bsrc]) c_bsrc / |c_bsrc| on adst
-                    const T br = __shfl_sync(0xffffffffu, reg_at(cr, bsrc >> 5), bsrc & 31);
-                    const T bi = __shfl_sync(0xffffffffu, reg_at(ci, bsrc >> 5), bsrc & 31);
-                    const T ra = __shfl_sync(0xffffffffu, reg_at(m, adst >> 5), adst & 31);
-                    const T m2 = br * br + bi * bi;
-                    if (m2 > T(0)) {
-                        const T f = (ra < T(0) ? T(-1) : T(1)) * m_rsqrt(m2);
-#pragma unroll
-                        for (int j = 0; j < NPL; ++j) {
-                            const bool hit = 32 * j + lane == adst;
-                            cr[j] = hit ? br * f : T(0);
-                            ci[j] = hit ? bi * f : T(0);
-                        }
-                    } else {
-                        al = -1;
-                    }
-                } else if (adst >= 0) {
-                    // zero frequency: every level pairs with itself, y_a = sqrt(gamma(0)) M_alpha[a][a] c_a
-                    const double *Md = p.tab.Mdiag + ((size_t)g * n + al) * N;
-                    T s = T(0);
-#pragma unroll
-                    for (int j = 0; j < NPL; ++j) {
-                        const int a = 32 * j + lane;
-                        const T d = a < N ? (T)Md[a] : T(0);
-                        cr[j] *= d;
-                        ci[j] *= d;
-                        s += cr[j] * cr[j] + ci[j] * ci[j];
-                    }
-                    s = warp_sum(s);
-                    if (s > T(0)) {
-                        const T inv = m_rsqrt(s);
-#pragma unroll
-                        for (int j = 0; j < NPL; ++j) {
-                            cr[j] *= inv;
-                            ci[j] *= inv;
-                        }
-                    } else {
-                        al = -1;
-                    }
-                }
-            }
-            if (bsrc < 0 || adst < 0) al = -1;
-        } else {
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) {
-                const int a = 32 * j + lane;
-                if (a < N) slow[a] = make_double2((double)cr[j], (double)ci[j]);
-            }
-            __syncwarp();
-            al = general_draw_apply(p, g, u1, u2, slow, slow + N, lane, &bsrc, &adst);
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) {
-                const int a = 32 * j + lane;
-                if (a < N) {
-                    cr[j] = (T)slow[a].x;
-                    ci[j] = (T)slow[a].y;
-                }
-            }
-            __syncwarp();
-        }
+        int bsrc = -1, adst = -1;
+        const int al = draw_apply<T, NPL>(p, g, cr, ci, u1, u2, lane, slow, &bsrc, &adst);
         if (al < 0) {
             ok = false;
             break;
         }
-        if (lane == 0) {
-            const unsigned long long idx = atomicAdd(p.jcount, 1ull);
-            if ((int64_t)idx < p.jcap) {
-                const double *lvlE = p.tab.lvlE + (size_t)g * N;
-                aqt_jump rec;
-                rec.traj = (int32_t)traj;
-                rec.grid = g;
-                rec.half = half;
-                rec.alpha = al;
-                rec.src = bsrc;
-                rec.dst = p.tab.mfirst[(size_t)g * N + adst];
-                rec.t = t_half0 + (p.tau - tau_rem) + t;
-                rec.omega = lvlE[bsrc] - lvlE[adst];
-                p.jumps[idx] = rec;
-            }
-        }
+        record_jump(p, traj, g, half, al, bsrc, adst, t_half0 + (p.tau - tau_rem) + t, lane);
         __syncwarp();
         logr = log(u3);
         ell0 = 0.0;
@@ -663,6 +692,52 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         }
     }
     ell = ell0 + log1p(dend);
+    __syncwarp();
+}
+
+// The jump of the fixed-step sampler (App. B.1): at the start of a frozen
+// half-step whose jump test fired, draw the channel with (u1, u2) and apply it
+// to the state (no deterministic evolution in this half-step); the state at
+// sre/sim (level a at [a * stride], any norm) is replaced by the normalised
+// post-jump state. Jump time: the start of the half-step.
+template <typename T, int NPL>
+static __device__ __forceinline__ void fixed_step_jump(const RunParams &p, int g, int half, int64_t traj, T *sre, T *sim,
+                                                       int stride, double u1, double u2, int lane, double2 *slow) {
+    const int N = p.N;
+    T cr[NPL], ci[NPL];
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+        const int a = 32 * j + lane;
+        const bool v = a < N;
+        cr[j] = v ? sre[(size_t)a * stride] : T(0);
+        ci[j] = v ? sim[(size_t)a * stride] : T(0);
+        s += cr[j] * cr[j] + ci[j] * ci[j];
+    }
+    s = warp_sum(s);
+    int al = -1, bsrc = -1, adst = -1;
+    if (s > T(0) && isfinite(s)) {
+        const T inv = m_rsqrt(s);
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            cr[j] *= inv;
+            ci[j] *= inv;
+        }
+        al = draw_apply<T, NPL>(p, g, cr, ci, u1, u2, lane, slow, &bsrc, &adst);
+    }
+    if (al < 0) {
+        if (lane == 0) atomicOr(p.status, kStatusNumeric);
+    } else {
+        record_jump(p, traj, g, half, al, bsrc, adst, half == 0 ? g * p.dt - p.tau : g * p.dt, lane);
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const int a = 32 * j + lane;
+            if (a < N) {
+                sre[(size_t)a * stride] = cr[j];
+                sim[(size_t)a * stride] = ci[j];
+            }
+        }
+    }
     __syncwarp();
 }
 
@@ -689,6 +764,25 @@ static __device__ __noinline__ void jump_half_step_ool(const RunParams &p, int g
         *nj = k;
     }
     __syncwarp();
+}
+
+template <typename T, int NPL>
+static __device__ __noinline__ void fixed_step_jump_ool(const RunParams &p, int g, int half, int64_t traj, T *sre,
+                                                        T *sim, int stride, double u1, double u2, int lane,
+                                                        double2 *slow) {
+    __syncwarp();
+    fixed_step_jump<T, NPL>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
+}
+
+template <typename T>
+static __device__ __forceinline__ void fixed_step_jump_any(const RunParams &p, int g, int half, int64_t traj, T *sre,
+                                                           T *sim, int stride, double u1, double u2, int lane,
+                                                           double2 *slow) {
+    const int N = p.N;
+    if (N <= 32) fixed_step_jump_ool<T, 1>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
+    else if (N <= 64) fixed_step_jump_ool<T, 2>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
+    else if (N <= 128) fixed_step_jump_ool<T, 4>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
+    else fixed_step_jump_ool<T, 8>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
 }
 
 // Register tile from N for the SIMT kernels (N <= 256).

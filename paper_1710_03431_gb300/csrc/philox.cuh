@@ -5,6 +5,8 @@
 //   key = (seed, 0x0000000171003431), counter = (trajectory, event, 0, 0);
 //   event 0 -> x0: first threshold r;  event j >= 1 -> x0: u1, x1: u2, x2: next r;
 //   uniform(x) = ((x >> 12) + 0.5) * 2^-52, strictly inside (0, 1).
+// Fixed-step sampler (App. B.1): counter (trajectory, piece, 1, 0) for frozen
+// half-step `piece` (0, 1, ... in time order) -> x0: jump test, x1: u1, x2: u2.
 #pragma once
 #include <cstdint>
 
@@ -45,6 +47,10 @@ __device__ __forceinline__ double uniform01(uint64_t x) {
 
 __device__ __forceinline__ Philox4 traj_event(uint64_t seed, int64_t traj, int64_t event) {
     return philox4x64_10((uint64_t)traj, (uint64_t)event, 0ull, 0ull, seed, 0x0000000171003431ull);
+}
+
+__device__ __forceinline__ Philox4 piece_draws(uint64_t seed, int64_t traj, int64_t piece) {
+    return philox4x64_10((uint64_t)traj, (uint64_t)piece, 1ull, 0ull, seed, 0x0000000171003431ull);
 }
 
 }  // namespace aqt

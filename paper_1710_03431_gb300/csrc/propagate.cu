@@ -72,7 +72,8 @@ __device__ __forceinline__ const double *ehalf_table<double>(const RunParams &p)
 // the rotation's own relative norm error, kept in *nerr.
 template <typename R>
 __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t traj, R *cre, R *cim, int LD,
-                          const R *eh, const double *d2s, Scalars sc, double2 *c64, int lane, float *nerr) {
+                          const R *eh, const double *d2s, const double *gam, Scalars sc, double2 *c64, int lane,
+                          float *nerr) {
     const int N = p.N;
     double nu = 0.0, f = 0.0;
     for (int a = lane; a < N; a += 32) {
@@ -88,6 +89,30 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
         return;
     }
     if (half == 0 && g > 0) *nerr = fmaxf(*nerr, (float)fabs(nu - 1.0));
+    if (p.timing == kTimingFixed) {
+        // App. B.1: jump with probability tau lambda, lambda = sum_b |c_b|^2 Gamma_b / nu
+        double lam = 0.0;
+        for (int a = lane; a < N; a += 32) {
+            const double re = cre[a * LD + t], im = cim[a * LD + t];
+            lam += (re * re + im * im) * gam[a];
+        }
+        lam = warp_sum(lam) / nu;
+        const Philox4 rnd = piece_draws(p.seed, traj, 2 * (int64_t)g + half - 1);
+        if (p.tau * lam > uniform01(rnd.x[0])) {
+            fixed_step_jump_any<R>(p, g, half, traj, cre + t, cim + t, LD, uniform01(rnd.x[1]), uniform01(rnd.x[2]),
+                                   lane, c64);
+            return;
+        }
+        const R scale = (R)(1.0 / sqrt(f));
+        for (int a = lane; a < N; a += 32) {
+            const R re = cre[a * LD + t], im = cim[a * LD + t];
+            const R er = eh[2 * a], ei = eh[2 * a + 1];
+            cre[a * LD + t] = (re * er - im * ei) * scale;
+            cim[a * LD + t] = (re * ei + im * er) * scale;
+        }
+        __syncwarp();
+        return;
+    }
     f /= nu;
     const double ell = sc.ell[t], logr = sc.logr[t];
     const double ell_new = ell + log(f);
@@ -117,7 +142,8 @@ __global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // shared-memory carve (all offsets multiples of 16 bytes)
     double *d2s = reinterpret_cast<double *>(smem);
-    double *logr = d2s + N;
+    double *gam = d2s + N;  // -2 Im K_aa: the level's total jump rate
+    double *logr = gam + N;
     double *ell = logr + TT;
     double *obs = ell + TT;                         // [kWarps][2]
     int *nj = reinterpret_cast<int *>(obs + 2 * kWarps);
@@ -146,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
     auto load_grid = [&](int g) {
         for (int a = tid; a < N; a += kThreads) {
             d2s[a] = p.tab.d2[(size_t)g * N + a];
+            gam[a] = -2.0 * p.tab.kdiag[((size_t)g * N + a) * 2 + 1];
             eh[2 * a] = eh_tab[((size_t)g * N + a) * 2];
             eh[2 * a + 1] = eh_tab[((size_t)g * N + a) * 2 + 1];
         }
@@ -183,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
     auto half_all = [&](int g, int half) {
         for (int t = warp; t < TT; t += kWarps) {
             if (t0 + t >= p.M) continue;
-            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, sc, c64, lane, &nerr);
+            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, gam, sc, c64, lane, &nerr);
         }
     };
 
@@ -291,7 +318,7 @@ size_t simt_smem_bytes(int N, int TT, int precision) {
     const int LD = TT + 4;
     const int KB = std::min(N, std::max(1, kChunkBytes / (int)(N * rs)));
     size_t b = 0;
-    b += (size_t)N * 8 + 2 * (size_t)TT * 8 + 2 * kWarps * 8;  // d2s, logr, ell, obs
+    b += 2 * (size_t)N * 8 + 2 * (size_t)TT * 8 + 2 * kWarps * 8;  // d2s, gam, logr, ell, obs
     b += (size_t)((TT + 3) & ~3) * 4;                           // nj
     b += 2 * (size_t)N * LD * rs;                               // cre, cim
     b += (size_t)KB * N * rs;                                   // O chunk

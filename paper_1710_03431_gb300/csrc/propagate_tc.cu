@@ -57,6 +57,8 @@ constexpr int kStages = 4;
 // of O, FP16 hi (two 4 KB blocks) then lo (two 4 KB blocks).
 constexpr uint32_t kStageBytes = 16384;
 constexpr int kSlots = kScratchSlots;
+constexpr int kPassBatch = 2;  // pass 1: chunks of 8 product columns whose TMEM loads are in flight together
+constexpr int kSumBatch = 3;   // partial-sum reductions interleaved
 constexpr long long kWaitLimit = 1ll << 22;           // polls, and
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait (~1 ms)
 // wait sites, reported as status bits 8.. next to kStatusTimeout
@@ -230,6 +232,7 @@ struct TcShared {
     int *nj, *flag, *list;
     int *plist, *pcount;  // trajectories whose product this step comes from the patch buffer
     float2 *cst;          // [N] one jumped state staged for its next-step product
+    float *d2gs;          // [N] |exp(-i K_aa tau)|^2 at the current grid point for the ground-manifold levels
     float *red;  // [4][NC/8][16] partial sums per TMEM lane quarter
     int *count;
     volatile int *abort_flag;
@@ -301,6 +304,26 @@ __device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// The same for B independent sets of 16 values, stage by stage (the shuffles
+// of the B chains are independent and overlap).
+template <int B>
+__device__ __forceinline__ void reduce_scatter16_multi(float (&v)[B][16], int lane, float (&out)[B]) {
+#pragma unroll
+    for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i)
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const float send = upper ? v[b][i] : v[b][i + n / 2];
+                const float keep = upper ? v[b][i + n / 2] : v[b][i];
+                v[b][i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) out[b] = v[b][0] + __shfl_xor_sync(0xffffffffu, v[b][0], 1);
+}
+
 __device__ __forceinline__ int scatter_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
@@ -337,7 +360,7 @@ __device__ __forceinline__ float2 rotate_row(const unsigned char *tile, const fl
 }
 
 template <int MH>  // 128-level blocks of the state (N = 128 MH)
-__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
+__global__ void __maxnreg__(144) propagate_tc(RunParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16, nchunk = NC / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -365,7 +388,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     S.plist = S.list + TT;
     S.pcount = S.plist + TT;
     S.cst = reinterpret_cast<float2 *>(S.pcount + 4);
-    S.red = reinterpret_cast<float *>(S.cst + N);
+    S.d2gs = reinterpret_cast<float *>(S.cst + N);
+    S.red = S.d2gs + N;
 
     const uint32_t bar_full = smem_u32(S.bars), bar_empty = bar_full + 8 * kStages;
     // rowsA / rowsB: the next operand's levels [0, N/2) / [N/2, N) are written and
@@ -646,6 +670,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             for (int h = 0; h < MH; ++h) {
                 e2r[h] = last ? L[h].x : L[h].x * L[h].x - L[h].y * L[h].y;
                 e2i[h] = last ? L[h].y : 2.f * L[h].x * L[h].y;
+                // the ground-manifold levels' decay factors for the observable below
+                // (read after the barriers of pass 1; the previous step's reads are done)
+                const int a = 128 * h + 32 * q + lane;
+                if (ch == 0 && a < gs) S.d2gs[a] = L[h].w;
             }
             // ---- single pass: per-trajectory sums over levels, and the next operand ----
             // D = kappa_{g-1} O c_{g-1}; the operand written now is D E^2 / kappa_{g-1}
@@ -727,75 +755,72 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                     }
                 } else {
                     // pass 1 of this phase's blocks of 128 levels: the operand rows of this
-                    // thread's level
+                    // thread's level. The TMEM loads of kPassBatch chunks (products, and for
+                    // block 1 the partial sums parked by block 0) are in flight together and
+                    // waited for once.
 #pragma unroll
                     for (int h = 0; h < MH; ++h) {
                         if (h < hlo || h >= hhi) continue;
-                        auto process = [&](int c, uint32_t (&r)[8]) {
-                            // v = D E^2 kinv per trajectory in packed FP32x2 arithmetic (the
-                            // same roundings as the scalar form), split into FP16 hi / lo
-                            const float4 k4 = *reinterpret_cast<const float4 *>(S.kinv + 4 * c);
-                            const float kj[4] = {k4.x, k4.y, k4.z, k4.w};
-                            const float2 e2 = make_float2(e2r[h], e2i[h]);
-                            const float w = L[h].z, d2w = L[h].w * L[h].z;
-                            uint32_t ph[4], pl[4];
-                            float ps[12];  // this level's share of sum |D|^2 kinv^2 (1, w, d2 w)
+                        const float2 e2 = make_float2(e2r[h], e2i[h]);
+                        const float w = L[h].z, d2w = L[h].w * L[h].z;
+                        const int a = 128 * h + 32 * q + lane;
+                        const uint32_t lbase = tmem + ((uint32_t)(32 * q) << 16);
+                        for (int c0 = c_begin; c0 < c_end; c0 += kPassBatch) {
+                            const int nb = min(kPassBatch, c_end - c0);  // warp-uniform
+                            uint32_t r[kPassBatch][8], o[kPassBatch][12];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
-                                const float2 f = __fmul2_rn(e2, make_float2(kj[j], kj[j]));  // (fr, fi)
-                                const float2 v = __ffma2_rn(make_float2(re, re), f,
-                                                            __fmul2_rn(make_float2(im, im), make_float2(-f.y, f.x)));
-                                split2p(v, ph[j], pl[j]);
-                                const float qv = fmaf(re, re, im * im) * (kj[j] * kj[j]);
-                                ps[j] = qv;
-                                ps[4 + j] = qv * w;
-                                ps[8 + j] = qv * d2w;
-                            }
-                            // park the partial sums in spare TMEM columns (the block-1 pass adds
-                            // its share to block 0's); the warp reductions run beside the next
-                            // rotation
-                            const uint32_t pa = tmem + ((uint32_t)(32 * q) << 16) + park + 12u * (uint32_t)c;
-                            if (h > 0) {
-                                uint32_t o[12];
-                                tmem_ld4_issue(pa, o);
-                                tmem_ld4_issue(pa + 4, o + 4);
-                                tmem_ld4_issue(pa + 8, o + 8);
-                                tmem_wait();
-#pragma unroll
-                                for (int i = 0; i < 12; ++i) {
-                                    asm volatile("" : "+r"(o[i]));
-                                    ps[i] += __uint_as_float(o[i]);
+                            for (int cc = 0; cc < kPassBatch; ++cc)
+                                if (cc < nb) {
+                                    tmem_ld8_issue(lbase + (uint32_t)(h * NC + 8 * (c0 + cc)), r[cc]);
+                                    if (h > 0) {
+                                        const uint32_t pa = lbase + park + 12u * (uint32_t)(c0 + cc);
+                                        tmem_ld4_issue(pa, o[cc]);
+                                        tmem_ld4_issue(pa + 4, o[cc] + 4);
+                                        tmem_ld4_issue(pa + 8, o[cc] + 8);
+                                    }
                                 }
+                            tmem_wait();
+#pragma unroll
+                            for (int cc = 0; cc < kPassBatch; ++cc) {
+                                if (cc >= nb) continue;
+                                reg_fence(r[cc]);
+                                const int c = c0 + cc;
+                                // v = D E^2 kinv per trajectory in packed FP32x2 arithmetic (the
+                                // same roundings as the scalar form), split into FP16 hi / lo
+                                const float4 k4 = *reinterpret_cast<const float4 *>(S.kinv + 4 * c);
+                                const float kj[4] = {k4.x, k4.y, k4.z, k4.w};
+                                uint32_t ph[4], pl[4];
+                                float ps[12];  // this level's share of sum |D|^2 kinv^2 (1, w, d2 w)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const float re = __uint_as_float(r[cc][2 * j]), im = __uint_as_float(r[cc][2 * j + 1]);
+                                    const float2 f = __fmul2_rn(e2, make_float2(kj[j], kj[j]));  // (fr, fi)
+                                    const float2 v = __ffma2_rn(make_float2(re, re), f,
+                                                                __fmul2_rn(make_float2(im, im), make_float2(-f.y, f.x)));
+                                    split2p(v, ph[j], pl[j]);
+                                    const float qv = fmaf(re, re, im * im) * (kj[j] * kj[j]);
+                                    ps[j] = qv;
+                                    ps[4 + j] = qv * w;
+                                    ps[8 + j] = qv * d2w;
+                                }
+                                // park the partial sums in spare TMEM columns (the block-1 pass adds
+                                // its share to block 0's); the warp reductions run beside the next
+                                // rotation
+                                if (h > 0) {
+#pragma unroll
+                                    for (int i = 0; i < 12; ++i) {
+                                        asm volatile("" : "+r"(o[cc][i]));
+                                        ps[i] += __uint_as_float(o[cc][i]);
+                                    }
+                                }
+                                const uint32_t pa = lbase + park + 12u * (uint32_t)c;
+                                tmem_st4(pa, ps);
+                                tmem_st4(pa + 4, ps + 4);
+                                tmem_st4(pa + 8, ps + 8);
+                                const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
+                                *reinterpret_cast<uint4 *>(sB_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                                *reinterpret_cast<uint4 *>(sB_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                             }
-                            tmem_st4(pa, ps);
-                            tmem_st4(pa + 4, ps + 4);
-                            tmem_st4(pa + 8, ps + 8);
-                            const int a = 128 * h + 32 * q + lane;
-                            const size_t off = ((size_t)(a >> 3) * (NC >> 3) + c) * 128 + (a & 7) * 16;
-                            *reinterpret_cast<uint4 *>(sB_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                            *reinterpret_cast<uint4 *>(sB_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-                        };
-                        auto issue = [&](int c, uint32_t (&r)[8]) {
-                            tmem_ld8_issue(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * NC + 8 * c), r);
-                        };
-                        // the loads of chunk c+1 are in flight while chunk c is processed
-                        uint32_t rA[8], rB[8];
-                        int c = c_begin;
-                        if (c < c_end) issue(c, rA);
-                        tmem_wait();
-                        reg_fence(rA);
-                        while (c < c_end) {
-                            if (c + 1 < c_end) issue(c + 1, rB);
-                            process(c, rA);
-                            tmem_wait();
-                            reg_fence(rB);
-                            if (++c >= c_end) break;
-                            if (c + 1 < c_end) issue(c + 1, rA);
-                            process(c, rB);
-                            tmem_wait();
-                            reg_fence(rA);
-                            ++c;
                         }
                     }
                 }
@@ -814,23 +839,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             // ---- warp reductions of the partial sums parked by pass 1, while the next
             // rotation runs (its products use other TMEM columns) ------------------------
             if (!last) {
-                for (int c = c_begin; c < c_end; ++c) {
-                    uint32_t o[12];
-                    const uint32_t pa = tmem + ((uint32_t)(32 * q) << 16) + park + 12u * (uint32_t)c;
-                    tmem_ld4_issue(pa, o);
-                    tmem_ld4_issue(pa + 4, o + 4);
-                    tmem_ld4_issue(pa + 8, o + 8);
-                    tmem_wait();
-                    float v16[16];
+                // kSumBatch chunks at a time: their TMEM loads in flight together, then
+                // their reductions interleaved (independent shuffle chains)
+                for (int c0 = c_begin; c0 < c_end; c0 += kSumBatch) {
+                    const int nb = min(kSumBatch, c_end - c0);  // warp-uniform
+                    uint32_t o[kSumBatch][12];
 #pragma unroll
-                    for (int i = 0; i < 12; ++i) {
-                        asm volatile("" : "+r"(o[i]));
-                        v16[i] = __uint_as_float(o[i]);
+                    for (int cc = 0; cc < kSumBatch; ++cc) {
+                        if (cc < nb) {
+                            const uint32_t pa = tmem + ((uint32_t)(32 * q) << 16) + park + 12u * (uint32_t)(c0 + cc);
+                            tmem_ld4_issue(pa, o[cc]);
+                            tmem_ld4_issue(pa + 4, o[cc] + 4);
+                            tmem_ld4_issue(pa + 8, o[cc] + 8);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 12; ++i) o[cc][i] = 0u;
+                        }
                     }
+                    tmem_wait();
+                    float v[kSumBatch][16];
 #pragma unroll
-                    for (int i = 12; i < 16; ++i) v16[i] = 0.0f;
-                    const float tot = reduce_scatter16(v16, lane);
-                    if ((lane & 1) == 0) S.red[((size_t)q * nchunk + c) * 16 + scatter_index(lane)] = tot;
+                    for (int cc = 0; cc < kSumBatch; ++cc) {
+#pragma unroll
+                        for (int i = 0; i < 12; ++i) {
+                            asm volatile("" : "+r"(o[cc][i]));
+                            v[cc][i] = __uint_as_float(o[cc][i]);
+                        }
+#pragma unroll
+                        for (int i = 12; i < 16; ++i) v[cc][i] = 0.0f;
+                    }
+                    float tot[kSumBatch];
+                    reduce_scatter16_multi<kSumBatch>(v, lane, tot);
+#pragma unroll
+                    for (int cc = 0; cc < kSumBatch; ++cc)
+                        if (cc < nb && (lane & 1) == 0)
+                            S.red[((size_t)q * nchunk + c0 + cc) * 16 + scatter_index(lane)] = tot[cc];
                 }
             }
             if (etid == 0) *S.count = 0;
@@ -856,7 +899,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                             const __half2 bh = *reinterpret_cast<const __half2 *>(sB_hi + off);
                             const __half2 bl = *reinterpret_cast<const __half2 *>(sB_lo + off);
                             const float br = __low2float(bh) + __low2float(bl), bi = __high2float(bh) + __high2float(bl);
-                            X += fmaf(br, br, bi * bi) / lvl[(size_t)g * N + a].w;
+                            X += fmaf(br, br, bi * bi) / S.d2gs[a];
                         }
                     }
                     S.P[t] = Pt;
@@ -1026,7 +1069,7 @@ size_t tc_smem_bytes(int N, int TT) {
     const int NC = 2 * TT, nchunk = NC / 8;
     size_t b = 2 * (size_t)N * NC * 2 + (size_t)kStages * kStageBytes;
     b += 8 * (2 * kStages + 4) + 16 + (size_t)TT * (8 * 2 + 4 * 4 + 4 * 4) + 16 +
-         (size_t)4 * nchunk * 16 * 4 + (size_t)N * 8;
+         (size_t)4 * nchunk * 16 * 4 + (size_t)N * 8 + (size_t)N * 4;
     b = (b + 1023) & ~(size_t)1023;
     // one CTA per SM: the kernel allocates tensor-memory columns without sharing
     return b < 120 * 1024 ? 120 * 1024 : b;

@@ -175,3 +175,51 @@ def test_rotation_norm_error_fp64_fp32(aqt_lib):
     assert 0.0 < r64["roterr"] < 1e-12
     assert 0.0 < r32["roterr"] < 1e-5
 
+
+
+def _compare_fixed_step(A, inst, res, M, t_tol, state_tol, min_identical):
+    p, oj, ofin = trajectories.sample_fixed_step(inst, list(range(M)))
+    gj, ojj = jumps_by_traj(res["jumps"]), jumps_by_traj(oj)
+    identical = 0
+    for t in range(M):
+        a, b = gj.get(t, []), ojj.get(t, [])
+        if len(a) == len(b) and all((x["grid"], x["half"], x["alpha"], x["src"], x["dst"]) ==
+                                    (y["grid"], y["half"], y["alpha"], y["src"], y["dst"]) and
+                                    abs(x["t"] - y["t"]) <= t_tol for x, y in zip(a, b)):
+            identical += 1
+            assert abs(abs(np.vdot(res["final"][t], ofin[t])) - 1.0) <= state_tol, t
+    assert identical >= min_identical * M, (identical, M)
+    return p, oj
+
+
+def test_fixed_step_sampler_fp64_every_trajectory(aqt_lib):
+    """The fixed-step unravelling of App. B.1 (a jump test with probability
+    tau lambda per half-step) against the oracle's, same random streams."""
+    A = aqt_lib
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=5.0, n_grid=101, seed=99)
+    M = 64
+    res = run_lib(A, inst, A.AQT_PREC_FP64, M=M, timing=A.AQT_JUMP_FIXED_STEP)
+    assert res["status"] == A.AQT_OK
+    p, oj = _compare_fixed_step(A, inst, res, M, t_tol=1e-12, state_tol=1e-10, min_identical=1.0)
+    assert len(oj) > 10 and len(res["jumps"]) == len(oj)
+    np.testing.assert_allclose(res["s1"], p.sum(axis=0), rtol=0, atol=1e-9)
+
+
+def test_fixed_step_sampler_fp32_and_ame(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(3, 45, eta_g2=0.02, t_f=6.0, n_grid=201, seed=4)
+    M = 300
+    res = run_lib(A, inst, A.AQT_PREC_FP32, M=M, timing=A.AQT_JUMP_FIXED_STEP)
+    assert res["status"] == A.AQT_OK
+    _compare_fixed_step(A, inst, res, M, t_tol=1e-12, state_tol=1e-5, min_identical=0.97)
+    ref = ame.run(inst)["p_gs"]
+    for k in (100, 200):
+        assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], se_bound(ref[k], M)) + 1e-6
+
+
+def test_fixed_step_sampler_not_on_tensor_cores(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(7, 3, n_grid=5)
+    with pytest.raises(A.AqtError) as e:
+        A.Session(inst, precision=A.AQT_PREC_F16SPLIT, M=16, timing=A.AQT_JUMP_FIXED_STEP).build()
+    assert e.value.status == A.AQT_EINVAL
