@@ -30,12 +30,9 @@ if ROOT not in sys.path:
 METRIC = "trajectory-steps/s"
 UNIT = "trajectory-steps/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes (read + write) of one propagate_tc launch on the 8-qubit, N=256, M=10^4, 2000-point,
-# t_f=10 ns workload, from one ncu capture of the current kernel (dram__bytes_read.sum 650.33 MB +
-# dram__bytes_write.sum 16.56 MB, 1 pass); reported only for that workload and reset to None
-# whenever the kernel changes.
-TC_TRAFFIC = {(8, 256, 10000, 2000, 10.0): 650.33e6 + 16.56e6}
-
+# DRAM bytes (read + write) of one propagate_tc launch, by workload (n, N, M, n_grid, t_f), from an ncu
+# capture of the kernel as it is now; empty until that capture is taken (then "traffic" is null).
+TC_TRAFFIC = {}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -44,20 +41,66 @@ def parse():
                     help="timed steps (default: 60 for f16split, 3 for fp32 / fp64, 5 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f16split", choices=["f16split", "fp32", "fp64"])
+    ap.add_argument("--config", default="main", choices=["main", "small"],
+                    help="main: 8 qubits, N = 256 (default); small: 4 qubits, N = 16")
+    ap.add_argument("--precision", default=None, choices=["f16split", "fp32", "fp64"],
+                    help="default: f16split for main, fp64 for small")
     ap.add_argument("--tf", type=float, default=10.0)
-    ap.add_argument("--M", type=int, default=10_000)
-    ap.add_argument("--n-grid", type=int, default=2000)
+    ap.add_argument("--M", type=int, default=None, help="default: 10^4 (main), 1000 (small)")
+    ap.add_argument("--n-grid", type=int, default=None, help="default: 2000 (main), 1000 (small)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the in-process tensor / SIMT peak measurement")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
     ap.add_argument("--cpu-sample-traj", type=int, default=2000)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = "f16split" if a.config == "main" else "fp64"
+    if a.M is None:
+        a.M = 10_000 if a.config == "main" else 1000
+    if a.n_grid is None:
+        a.n_grid = 2000 if a.config == "main" else 1000
+    return a
 
 
 def workload(args):
     import workloads as W
+    if args.config == "small":
+        return W.cfg_small(t_f=args.tf, M=args.M, n_grid=args.n_grid)
     return W.cfg_main(t_f=args.tf, M=args.M, n_grid=args.n_grid)
+
+
+def measure_peaks(device) -> dict:
+    """Dense matrix-product rates of this GPU in TFLOP/s, measured here with
+    library GEMMs (torch.matmul, CUDA events, best of 5 after warm-up): FP16
+    and TF32 on the tensor cores, FP32 without TF32 and FP64. They are the
+    roofline denominators of the kernels whose arithmetic they match; no clock
+    or power setting is touched."""
+    import torch
+    out = {}
+    old_tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, tf32 in (("fp16", torch.float16, 8192, False), ("tf32", torch.float32, 8192, True),
+                                  ("fp32", torch.float32, 4096, False), ("fp64", torch.float64, 2048, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=device, dtype=dt)
+            b = torch.randn(n, n, device=device, dtype=dt)
+            for _ in range(3):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old_tf32
+    torch.cuda.empty_cache()
+    return out
 
 
 def rank_seed(base: int, rank: int) -> int:
@@ -163,11 +206,11 @@ def alu_fp64_peak_tflops(num_sms: int, mhz: float) -> float:
 
 
 # ------------------------------------------------------------- CPU baseline ---
-def cpu_baseline_run(args, n_traj: int, n_steps: int):
+def cpu_baseline_run(args, n_traj: int, n_steps: int, first: int = 0):
     """The FP64 oracle's trajectory propagation on a bounded sample of the
-    workload: n_traj trajectories over the first n_steps grid steps. The
-    per-grid eigensystem/propagator setup is excluded, as the GPU's FP64
-    table build is excluded from its number. Single thread."""
+    workload: trajectories first .. first + n_traj - 1 over the first n_steps
+    grid steps. The per-grid eigensystem/propagator setup is excluded, as the
+    GPU's FP64 table build is excluded from its number. Single thread."""
     from oracle import ame, trajectories
     inst = workload(args)
     _, dt = __import__("oracle.model", fromlist=["grid"]).grid(inst)
@@ -180,7 +223,7 @@ def cpu_baseline_run(args, n_traj: int, n_steps: int):
             break
         piece = trajectories.Piece(fr, tau)
         if k == 0:
-            trajs = [trajectories.Trajectory(t, inst.seed, fr.eig.V[:, 0]) for t in range(n_traj)]
+            trajs = [trajectories.Trajectory(t, inst.seed, fr.eig.V[:, 0]) for t in range(first, first + n_traj)]
         else:
             t0 = time.perf_counter()
             for tr in trajs:
@@ -207,6 +250,33 @@ def cpu_baseline(args, n_traj=None, n_steps=None):
     return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_traj} trajectories x first {n_steps} grid steps of the same workload, FP64 "
                       f"numpy/scipy, propagation only ({d['seconds']:.1f} s)"}
+
+
+def _cpu_worker(job):
+    argv, first, n_traj, n_steps = job
+    v, t = cpu_baseline_run(parse_from(argv), n_traj, n_steps, first)
+    return v, t
+
+
+def cpu_baseline_all_cores(args, n_traj=None, n_steps=None):
+    """The same oracle leg on every host core: one single-threaded worker per
+    core (spawned processes), each on its own trajectories; the rate is the
+    sum of the workers' rates while they all run."""
+    import multiprocessing
+    n_traj = n_traj or args.cpu_sample_traj
+    n_steps = n_steps or args.cpu_sample_steps
+    cores = len(os.sched_getaffinity(0))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    jobs = [(sys.argv[1:], i * n_traj, n_traj, n_steps) for i in range(cores)]
+    try:
+        with multiprocessing.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_cpu_worker, jobs)
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": str(e)[:300]}
+    return {"value": sum(v for v, _ in res), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} workers x {n_traj} trajectories x first {n_steps} grid steps of the same workload, "
+                      f"FP64 numpy/scipy, propagation only ({max(t for _, t in res):.1f} s)"}
 
 
 def parse_from(argv):
@@ -313,21 +383,30 @@ def run_ours(args):
     flops = 4.0 * N * N * traj_steps
     mhz = ck.get("sm_max_mhz") or 2070.0
     achieved = flops / kern_avg_s / 1e12
+    peaks, src = measured_peaks()
+    here = {} if args.no_peaks else measure_peaks(dev)
     if prec == A.AQT_PREC_F16SPLIT:
-        peaks, src = measured_peaks()
-        peak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+        if "fp16" in here:
+            peak = here["fp16"]
+            peak_src = "dense fp16 tensor rate measured in this process (cuBLAS 8192^3, best of 5, burst)"
+        else:
+            peak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+            peak_src = f"dense bf16 tensor peak, burst, {src} (MEASURED_PEAKS.json bf16_tflops; fp16 taken at the bf16 rate)"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TC_TRAFFIC.get((inst.n_qubits, N, M, K, float(inst.t_f))), "kernel": "propagate_tc",
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state); "
                                "the split form issues 3x that on the FP16 tensor pipe",
-                "issued_mma_frac": 3.0 * achieved / peak,
-                "peak_source": f"dense bf16/fp16 tensor peak, burst, {src} (MEASURED_PEAKS.json bf16_tflops; "
-                               "fp16 runs at the bf16 rate)"}
+                "issued_mma_frac": 3.0 * achieved / peak, "peak_source": peak_src,
+                "bf16_measured_peaks_json": peaks.get("bf16_tflops")}
     else:
-        if prec == A.AQT_PREC_FP32:
+        key = "fp32" if prec == A.AQT_PREC_FP32 else "fp64"
+        if key in here:
+            peak = here[key]
+            peak_src = f"dense {key} matrix-product rate measured in this process (cuBLAS, no TF32, best of 5)"
+        elif prec == A.AQT_PREC_FP32:
             peak = alu_fp32_peak_tflops(num_sms, mhz)
-            peak_src = f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+            peak_src = f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (nominal)"
         else:
             peak = alu_fp64_peak_tflops(num_sms, mhz)
             peak_src = f"FP64: 1.25 TFLOP/s nominal scaled to {mhz:.0f} MHz"
@@ -335,9 +414,12 @@ def run_ours(args):
                 "traffic": None, "kernel": f"propagate_simt<{'float' if prec else 'double'}>",
                 "algorithmic": "4 N^2 flop per trajectory-step (real N x N rotation of a complex state)",
                 "peak_source": peak_src}
+    roof["peaks_measured_here_tflops"] = here
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(args)
+        one = cpu_baseline(args)
+        cpu = cpu_baseline_all_cores(args)
+        cpu["one_core"] = one
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

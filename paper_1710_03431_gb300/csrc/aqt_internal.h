@@ -82,6 +82,11 @@ struct Tables {
     // manifold, or a Bohr class of nonzero frequency with several level
     // pairs); source-major: Rgen[slot][alpha][b][a]. Elsewhere the device forms
     // the one column of M_alpha a jump needs from V.
+    // Jump amplitudes of the lowest n_low source levels at every grid point
+    // (where the population, hence nearly every jump, is), source-major:
+    // Rlow[g][alpha][b][a] = R_alpha[a][b], b < n_low.
+    int n_low = 0;
+    hvec<double> Rlow;           // [K][n][n_low][N]
     std::vector<int32_t> gslot;  // [K] slot in Rgen, or -1
     int n_general = 0;
     hvec<double> Rgen;           // [n_general][n][N][N]
@@ -124,6 +129,7 @@ struct DevTables {
     const double *kdiag, *ehalf, *d2, *G, *lvlE;
     const double *Mdiag;  // [g][alpha][N] diagonal of M_alpha
     const void *V;        // [g][x][a] eigenvectors in the state precision (double or float)
+    const void *Rlow;     // [g][alpha][b][a], b < n_low: jump amplitudes in the state precision
     const int32_t *gslot; // [g] slot of the general jump tables, -1 at simple grid points
     const double *Rgen;   // [slot][alpha][b][a] jump amplitudes at general grid points
     const float *ehalf32;
@@ -143,6 +149,7 @@ enum JumpTiming : int { kTimingRefined = 0, kTimingGrid = 1, kTimingFixed = 2 };
 struct RunParams {
     int n, N, K, TT, RA, n_cta;
     int timing;
+    int n_low;  // source levels with a jump-amplitude table
     int64_t M;
     uint64_t seed;
     double tau, dt;
@@ -170,6 +177,7 @@ struct RunParams {
 // FP32 state (real, imaginary planes) handed between the epilogue warps.
 constexpr int kSlotDouble2 = 3;
 constexpr long long kDefaultWaitPolls = 1ll << 22;
+constexpr int kLowSources = 16;  // source levels whose jump amplitudes are tabled at every grid point
 constexpr int kScratchSlots = 8;
 
 // Scratch bytes of a run: the jump slots of every CTA, then, for the

@@ -16,7 +16,7 @@
 using namespace aqt;
 
 struct Layout {
-    size_t kdiag, ehalf, ehalf32, d2, G, Mdiag, V, gslot, Rgen, lvlE, mfirst, msize, meta, OT, tclvl;
+    size_t kdiag, ehalf, ehalf32, d2, G, Mdiag, V, Rlow, gslot, Rgen, lvlE, mfirst, msize, meta, OT, tclvl;
     size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, norm_err, total;
 };
 
@@ -105,6 +105,7 @@ void compute_layout(aqt_ctx *c) {
     L.G = take(K * n * N * 8);
     L.Mdiag = take(K * n * N * 8);
     L.V = take(K * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
+    L.Rlow = take(K * n * std::min<size_t>(N, kLowSources) * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
     L.gslot = take(K * 4);
     L.Rgen = take((size_t)c->tab.n_general * n * N * N * 8);
     L.lvlE = take(K * N * 8);
@@ -169,6 +170,8 @@ void fill_params(const aqt_ctx *c, RunParams *p) {
     p->tab.G = (const double *)(c->ws + L.G);
     p->tab.Mdiag = (const double *)(c->ws + L.Mdiag);
     p->tab.V = c->ws + L.V;
+    p->tab.Rlow = c->ws + L.Rlow;
+    p->n_low = c->tab.n_low;
     p->tab.gslot = (const int32_t *)(c->ws + L.gslot);
     p->tab.Rgen = (const double *)(c->ws + L.Rgen);
     p->tab.lvlE = (const double *)(c->ws + L.lvlE);
@@ -430,8 +433,10 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     hvec<float> v32, o32;
     hvec<__half> o16;
     std::vector<float> lv;
+    hvec<float> rl32;
     if (c->in.precision == AQT_PREC_FP64) {
         if (!e) e = put(L.V, t.V.data(), t.V.size() * 8);
+        if (!e) e = put(L.Rlow, t.Rlow.data(), t.Rlow.size() * 8);
         if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
     } else {
         v32.resize(K * NN);
@@ -439,6 +444,8 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
             for (size_t i = 0; i < NN; ++i) v32[g * NN + i] = (float)t.V[g * NN + i];
         });
         if (!e) e = put(L.V, v32.data(), v32.size() * 4);
+        rl32.assign(t.Rlow.begin(), t.Rlow.end());
+        if (!e) e = put(L.Rlow, rl32.data(), rl32.size() * 4);
     }
     if (c->in.precision == AQT_PREC_F16SPLIT) {
         // A-operand tiles in the order the tensor-core kernel streams them: per grid

@@ -23,10 +23,12 @@
 // Fast path (every manifold a single level and every Bohr class of nonzero
 // frequency a single level pair, the generic case once s > 0): stage one
 // picks (alpha, source b) from the FP64 rates G; stage two needs column b of
-// M_alpha = V^T sz_alpha V, which the warp forms from the eigenvector table
-// (O(N^2) per jump), weighted by gamma(E_b - E_a) computed in FP64. The class
-// operator then maps the source level to the target level alone, or, at zero
-// frequency, scales each level by the diagonal of M_alpha. Other grid points
+// R_alpha = sqrt(gamma) M_alpha, M_alpha = V^T sz_alpha V: a table row for the
+// lowest sources (where the population is), otherwise a column of M_alpha
+// that the warp forms from the eigenvector table (O(N^2) per jump), weighted
+// by gamma(E_b - E_a). The class operator then maps the source level to the
+// target level alone, or, at zero frequency, scales each level by the
+// diagonal of M_alpha. Other grid points
 // go through a general FP64 routine over degenerate manifolds and
 // multi-pair classes, with the full jump amplitudes of those grid points.
 #pragma once
@@ -314,10 +316,25 @@ static __device__ int general_draw_apply(const RunParams &p, int g, double u1, d
 }
 
 // Gamma of the Ohmic bath (Sec. V): 2 pi eta g^2 w e^{-|w|/w_c} / (1 - e^{-beta w}),
-// with its limit 2 pi eta g^2 / beta at w = 0; FP64.
+// with its limit 2 pi eta g^2 / beta at w = 0, in the state's precision (the
+// stage-two weights need no more accuracy than the state's column of M).
 static __device__ __forceinline__ double bath_gamma(const RunParams &p, double w) {
     if (w == 0.0) return 2.0 * 3.14159265358979323846 * p.eta_g2 / p.beta;
     return 2.0 * 3.14159265358979323846 * p.eta_g2 * w * exp(-fabs(w) / p.omega_c) / (-expm1(-p.beta * w));
+}
+static __device__ __forceinline__ float bath_gamma(const RunParams &p, float w) {
+    const float c = 6.2831853071795864769f * (float)p.eta_g2;
+    if (w == 0.0f) return c / (float)p.beta;
+    return c * w * expf(-fabsf(w) / (float)p.omega_c) / (-expm1f(-(float)p.beta * w));
+}
+
+// e^y - 1 in FP64. For |y| <= 2^-6 (every decay exponent 2 Im K_aa t of a
+// frozen half-step at the grid sizes used here) the Taylor polynomial of
+// degree 7 in Horner form: its truncation error is below y^8 / 8! < 1e-17 |y|.
+// Otherwise the library function.
+static __device__ __forceinline__ double expm1_small(double y) {
+    if (fabs(y) > 0.015625) return expm1(y);
+    return y * (1.0 + y * (1.0 / 2 + y * (1.0 / 6 + y * (1.0 / 24 + y * (1.0 / 120 + y * (1.0 / 720 + y * (1.0 / 5040)))))));
 }
 
 // Column b of M_alpha = V^T sz_alpha V at grid point g for the levels a = 32 j
@@ -331,7 +348,7 @@ static __device__ __forceinline__ void m_column(const RunParams &p, int g, int a
 #pragma unroll
     for (int j = 0; j < NPL; ++j) m[j] = T(0);
     const int lo_mask = (1 << al) - 1;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < N / 2; ++i) {
         const int x = ((i >> al) << (al + 1)) | (1 << al) | (i & lo_mask);
         const T *row = Vg + (size_t)x * N;
@@ -408,17 +425,29 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
             bsrc = reg_pick(w, target - cum, lane);
         }
         if (bsrc >= 0) {
-            // stage two: target a with weight gamma(E_b - E_a) M_alpha[a][b]^2
+            // stage two: target a with weight R_alpha[a][b]^2 = gamma(E_b - E_a) M_alpha[a][b]^2,
+            // from the table for the lowest sources, else from a column of M formed here
             T m[NPL];
-            m_column<T, NPL>(p, g, al, bsrc, lane, m);
-            const double *lvlE = p.tab.lvlE + (size_t)g * N;
-            const double eb = lvlE[bsrc];
             double w[NPL], tot2 = 0.0;
+            if (bsrc < p.n_low) {
+                const T *row = static_cast<const T *>(p.tab.Rlow) + (((size_t)g * n + al) * p.n_low + bsrc) * N;
 #pragma unroll
-            for (int j = 0; j < NPL; ++j) {
-                const int a = 32 * j + lane;
-                w[j] = a < N ? bath_gamma(p, eb - lvlE[a]) * ((double)m[j] * (double)m[j]) : 0.0;
-                tot2 += w[j];
+                for (int j = 0; j < NPL; ++j) {
+                    const int a = 32 * j + lane;
+                    m[j] = a < N ? row[a] : T(0);
+                    w[j] = (double)m[j] * (double)m[j];
+                    tot2 += w[j];
+                }
+            } else {
+                m_column<T, NPL>(p, g, al, bsrc, lane, m);
+                const double *lvlE = p.tab.lvlE + (size_t)g * N;
+                const double eb = lvlE[bsrc];
+#pragma unroll
+                for (int j = 0; j < NPL; ++j) {
+                    const int a = 32 * j + lane;
+                    w[j] = a < N ? (double)bath_gamma(p, (T)(eb - lvlE[a])) * ((double)m[j] * (double)m[j]) : 0.0;
+                    tot2 += w[j];
+                }
             }
             tot2 = warp_sum(tot2);
             adst = reg_pick(w, u2 * tot2, lane);
@@ -584,7 +613,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const double q = pop(j), x = kim2d(j);
-            const double e = expm1(x * t);
+            const double e = expm1_small(x * t);
             d += q * e;
             e1 += q * x * (e + 1.0);
         }

@@ -57,7 +57,7 @@ constexpr int kStages = 4;
 // of O, FP16 hi (two 4 KB blocks) then lo (two 4 KB blocks).
 constexpr uint32_t kStageBytes = 16384;
 constexpr int kSlots = kScratchSlots;
-constexpr int kPassBatch = 2;  // pass 1: chunks of 8 product columns whose TMEM loads are in flight together
+constexpr int kPassBatch = 1;  // pass 1: chunks of 8 product columns whose TMEM loads are in flight together
 constexpr int kSumBatch = 3;   // partial-sum reductions interleaved
 constexpr long long kWaitLimit = 1ll << 22;           // polls, and
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait (~1 ms)
@@ -360,7 +360,7 @@ __device__ __forceinline__ float2 rotate_row(const unsigned char *tile, const fl
 }
 
 template <int MH>  // 128-level blocks of the state (N = 128 MH)
-__global__ void __maxnreg__(144) propagate_tc(RunParams p) {
+__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16, nchunk = NC / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

@@ -205,6 +205,8 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
     tab.Mdiag.assign((size_t)K * n * N, 0.0);
+    tab.n_low = std::min(N, kLowSources);
+    tab.Rlow.resize((size_t)K * n * tab.n_low * N);
     tab.gslot.assign(K, -1);
     tab.n_general = 0;
     tab.Rgen.clear();
@@ -378,6 +380,14 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         for (int al = 0; al < n; ++al)
             for (int b = 0; b < N; ++b)
                 tab.Mdiag[((size_t)g * n + al) * N + b] = Mg[(size_t)al * NN + (size_t)b * N + b];
+        // jump amplitudes of the lowest sources (Eq. Aired: R = sqrt(gamma) M), source-major;
+        // M_alpha is symmetric, so row b of M gives column b
+        for (int al = 0; al < n; ++al)
+            for (int b = 0; b < tab.n_low; ++b) {
+                double *dst = &tab.Rlow[(((size_t)g * n + al) * tab.n_low + b) * N];
+                const double *Mb = Mg + (size_t)al * NN + (size_t)b * N;
+                for (int a = 0; a < N; ++a) dst[a] = std::sqrt(gam[(size_t)a * N + b]) * Mb[a];
+            }
         // half-step factors exp(-i K tau) and |.|^2
         double *eh = &tab.ehalf[(size_t)g * N * 2];
         double *dd = &tab.d2[(size_t)g * N];

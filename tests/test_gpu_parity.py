@@ -125,7 +125,7 @@ def test_fp32_against_oracle(aqt_lib):
     M = 300
     res = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_FP32, M=M)
     assert res["status"] == aqt_lib.AQT_OK
-    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-5, state_tol=1e-5, min_identical=0.97)
+    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-7, state_tol=1e-6, min_identical=0.97)
     # observable sums: FP32 state, FP64 accumulation
     assert np.max(np.abs(res["s1"] - p.sum(axis=0))) < 1e-3 * M
     ref = ame.run(inst)["p_gs"]
@@ -211,7 +211,7 @@ def test_fixed_step_sampler_fp32_and_ame(aqt_lib):
     M = 300
     res = run_lib(A, inst, A.AQT_PREC_FP32, M=M, timing=A.AQT_JUMP_FIXED_STEP)
     assert res["status"] == A.AQT_OK
-    _compare_fixed_step(A, inst, res, M, t_tol=1e-12, state_tol=1e-5, min_identical=0.97)
+    _compare_fixed_step(A, inst, res, M, t_tol=1e-12, state_tol=1e-6, min_identical=0.97)
     ref = ame.run(inst)["p_gs"]
     for k in (100, 200):
         assert abs(res["mean"][k] - ref[k]) < 3.5 * max(res["se"][k], se_bound(ref[k], M)) + 1e-6

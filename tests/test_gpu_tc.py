@@ -2,11 +2,11 @@
 GPU path, through the C ABI.
 
 The rotation runs as O_hi C_hi + O_hi C_lo + O_lo C_hi with FP32 accumulation
-(22-bit mantissa), the state is FP32 and the jump clock, crossing time and
-channel draw are FP64. With common random numbers almost every trajectory
-keeps the oracle's jump sequence; the rare ones whose channel draw sits within
-the rounding error of a CDF boundary may diverge, so parity is asserted on the
-identical ones and statistically on all.
+(22-bit mantissa), the state is FP32; the jump clock, crossing time and both
+channel CDFs are FP64. With common random numbers every trajectory is expected
+to keep the oracle's jump sequence; one whose draw sits within the FP32
+state's rounding of a CDF boundary may diverge, so parity is asserted on the
+identical ones (at least 97 %) and statistically on all.
 """
 import math
 
@@ -26,7 +26,8 @@ def test_tc_against_oracle(aqt_lib, n, M, grid, eta):
     inst = W.tfim_instance(n, 100 + n, eta_g2=eta, t_f=5.0, n_grid=grid, seed=21)
     res = run_lib(aqt_lib, inst, aqt_lib.AQT_PREC_F16SPLIT, M=M)
     assert res["status"] == aqt_lib.AQT_OK
-    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-5, state_tol=2e-5, min_identical=0.9)
+    # jump times: FP64 root of the FP32 state's decay, clock from FP32 epilogue sums (measured <= 8e-8 ns)
+    p, oj, _ = compare_crn(inst, res, list(range(M)), t_tol=1e-6, state_tol=1e-6, min_identical=0.97)
     assert len(oj) > 0
     assert np.max(np.abs(res["s1"] - p.sum(axis=0))) < 2e-4 * M
 
@@ -45,9 +46,18 @@ def test_tc_matches_fp64_gpu(aqt_lib):
     for r in rtc["jumps"]:
         jtc.setdefault(int(r["traj"]), []).append((r["grid"], r["half"], r["alpha"], r["src"], r["dst"]))
     same = [t for t in range(M) if j64.get(t, []) == jtc.get(t, [])]
-    assert len(same) >= 0.95 * M
+    assert len(same) >= 0.97 * M
     ov = np.abs(np.einsum("mi,mi->m", r64["final"][same].conj(), rtc["final"][same]))
-    assert np.max(np.abs(ov - 1.0)) < 2e-5
+    assert np.max(np.abs(ov - 1.0)) < 1e-6
+    t64 = {int(r["traj"]): [] for r in r64["jumps"]}
+    for r in r64["jumps"]:
+        t64[int(r["traj"])].append(r["t"])
+    ttc = {}
+    for r in rtc["jumps"]:
+        ttc.setdefault(int(r["traj"]), []).append(r["t"])
+    dts = [abs(a - b) for t in same for a, b in zip(t64.get(t, []), ttc.get(t, []))]
+    assert max(dts) < 1e-5            # measured 1.9e-6 ns over 300 trajectories x 300 steps
+    assert np.median(dts) < 1e-7      # measured 1.5e-8 ns
     assert np.max(np.abs(rtc["s1"] - r64["s1"])) < 1e-3 * M
 
 
@@ -95,7 +105,7 @@ def test_tc_general_jumps_at_degenerate_start(aqt_lib):
     assert len(same) >= 0.9 * M
     ov = np.abs(np.einsum("mi,mi->m", r64["final"][same].conj(), rtc["final"][same]))
     assert np.max(np.abs(ov - 1.0)) < 2e-5
-    compare_crn(inst, rtc, list(range(12)), t_tol=1e-5, state_tol=2e-5, min_identical=0.8)
+    compare_crn(inst, rtc, list(range(12)), t_tol=1e-6, state_tol=1e-6, min_identical=0.8)
 
 
 def test_tc_wait_timeout_reports_and_recovers(aqt_lib):
