@@ -41,11 +41,14 @@ def parse():
                     help="timed steps (default: 60 for f16split, 3 for fp32 / fp64, 5 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="main", choices=["main", "small"],
-                    help="main: 8 qubits, N = 256 (default); small: 4 qubits, N = 16")
+    ap.add_argument("--config", default="main", choices=["main", "small", "batch"],
+                    help="main: 8 qubits, N = 256 (default); small: 4 qubits, N = 16; batch: 64 instances of "
+                         "6-8 qubits in one batched launch")
+    ap.add_argument("--batch-qubits", default="6,7,8", help="batch: qubit counts cycled over the instances")
+    ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--precision", default=None, choices=["f16split", "fp32", "fp64"],
                     help="default: f16split for main, fp64 for small")
-    ap.add_argument("--tf", type=float, default=10.0)
+    ap.add_argument("--tf", type=float, default=None, help="default: 10 ns (main, small), 20 ns (batch)")
     ap.add_argument("--M", type=int, default=None, help="default: 10^4 (main), 1000 (small)")
     ap.add_argument("--n-grid", type=int, default=None, help="default: 2000 (main), 1000 (small)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the in-process tensor / SIMT peak measurement")
@@ -55,11 +58,13 @@ def parse():
     ap.add_argument("--cpu-sample-traj", type=int, default=2000)
     a = ap.parse_args()
     if a.precision is None:
-        a.precision = "f16split" if a.config == "main" else "fp64"
+        a.precision = "fp64" if a.config == "small" else "f16split"
     if a.M is None:
-        a.M = 10_000 if a.config == "main" else 1000
+        a.M = {"main": 10_000, "small": 1000, "batch": 2048}[a.config]
     if a.n_grid is None:
         a.n_grid = 2000 if a.config == "main" else 1000
+    if a.tf is None:
+        a.tf = 20.0 if a.config == "batch" else 10.0
     return a
 
 
@@ -471,10 +476,105 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ batch -----
+def run_batch(args):
+    """Many instances of uneven size in one batch (aqt_batch_run: one CUDA
+    graph with one persistent launch per kernel form). precision f16split:
+    members with N = 128 / 256 on the tensor cores, the others SIMT FP32;
+    fp32 / fp64: every member SIMT in that precision. One bench step = one
+    run of every member over its whole grid."""
+    import torch
+
+    import workloads as W
+    from paper_1710_03431_gb300 import aqt as A
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if args.steps is None:
+        args.steps = 5
+    qubits = tuple(int(x) for x in args.batch_qubits.split(","))
+    insts = W.cfg_batch(n_instances=args.batch_instances, qubits=qubits, M=args.M, n_grid=args.n_grid, t_f=args.tf)
+    sessions = []
+    t0 = time.perf_counter()
+    for inst in insts:
+        N = 1 << inst.n_qubits
+        if args.precision == "f16split":
+            prec = A.AQT_PREC_F16SPLIT if N in (128, 256) else A.AQT_PREC_FP32
+        else:
+            prec = {"fp32": A.AQT_PREC_FP32, "fp64": A.AQT_PREC_FP64}[args.precision]
+        S = A.Session(inst, precision=prec, device=local, seed=rank_seed(inst.seed, rank))
+        S.build()
+        sessions.append(S)
+    torch.cuda.synchronize()
+    table_s = time.perf_counter() - t0
+    b = A.aqt_batch_create([S.ctx for S in sessions])
+    ws = torch.empty(A.aqt_batch_workspace_size(b), dtype=torch.uint8, device=f"cuda:{local}")
+    A.aqt_batch_bind_workspace(b, ws.data_ptr(), ws.numel())
+    stream = torch.cuda.current_stream()
+    t1 = time.perf_counter()
+    A.aqt_batch_tune(b, stream.cuda_stream)
+    tune_s = time.perf_counter() - t1
+    for _ in range(args.warmup):
+        A.aqt_batch_run(b, stream.cuda_stream)
+        A.aqt_batch_sync(b, len(sessions))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        A.aqt_batch_run(b, stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    st, member = A.aqt_batch_sync(b, len(sessions))
+    ck = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        elapsed_ms = max_over_ranks(elapsed_ms, torch.device(f"cuda:{local}"))
+    ms_per_step = elapsed_ms / args.steps
+    traj_steps = sum(S.M * (S.K - 1) for S in sessions)
+    flops = sum(4.0 * S.N * S.N * S.M * (S.K - 1) for S in sessions)
+    shapes = [A.aqt_batch_get_shape(b, i) for i in range(len(sessions))]
+    if rank != 0:
+        return
+    forms = {}
+    for S, sh in zip(sessions, shapes):
+        key = ["simt-fp64", "simt-fp32", "tensor-f16x3"][sh[0]] + f"-N{S.N}"
+        f = forms.setdefault(key, {"instances": 0, "tt": sh[1], "ra_or_mh": sh[2], "tiles": 0})
+        f["instances"] += 1
+        f["tiles"] += sh[3]
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": world * traj_steps / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f16split": "f16x3-f32acc+f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"tfim-batch-{len(insts)}x{'/'.join(map(str, qubits))}q-M{insts[0].M}-"
+                               f"grid{insts[0].n_grid}-tf{insts[0].t_f:g}ns",
+                   "instances": len(insts), "qubits": list(qubits), "M_each": insts[0].M,
+                   "n_grid": insts[0].n_grid, "t_f_ns": insts[0].t_f, "precision": args.precision,
+                   "launch": "one CUDA graph per run: counter resets, one persistent kernel per form, reduction",
+                   "forms": forms},
+        "roofline": {"bound": "mixed", "achieved": achieved, "unit": "TFLOP/s",
+                     "algorithmic": "4 N^2 flop per trajectory-step summed over the members"},
+        "status": A.STATUS_NAMES.get(st, st), "clocks": ck, "table_build_s": table_s, "tune_s": tune_s,
+        "gpu_launches": args.steps * (1 + len(forms)),
+    }
+    print(json.dumps(line))
+    A.aqt_batch_destroy(b)
+    for S in sessions:
+        S.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

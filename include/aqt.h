@@ -140,9 +140,8 @@ aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int prec
                                 int64_t jump_capacity);
 
 /* Device bytes the caller must provide for the current inputs. Device runs
- * take n_qubits <= 8 (N <= 256: the jump warp keeps N/32 levels per lane in
- * registers) and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise AQT_EINVAL
- * (host-only contexts build tables up to n_qubits = 10). The size depends on
+ * take n_qubits <= 10 (N <= 1024; the jump warp keeps N/32 levels per lane)
+ * and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise AQT_EINVAL. The size depends on
  * the spectrum (full jump amplitudes are kept for the grid points with
  * degenerate levels or coinciding Bohr frequencies), so this call builds the
  * host tables of aqt_build_tables if they are not built yet, and can return
@@ -202,6 +201,14 @@ aqt_status aqt_get_observables(aqt_ctx *ctx, double *mean, double *stderr_);
 /* Raw FP64 sums over trajectories, sum_x[n_grid] and sum_x2[n_grid]. */
 aqt_status aqt_get_observable_sums(aqt_ctx *ctx, double *sum_x, double *sum_x2);
 
+/* Mean and standard error of the mean (Sec. VI.A, Eq. stderror,
+ * sigma^2 = sum (x - mean)^2 / (M (M - 1))) from raw sums over M trajectories:
+ * the statistics of aqt_get_observables for sums merged across contexts or
+ * ranks (trajectories sharded over several GPUs add their sums; the merge is
+ * one sum of 2 n_grid doubles per rank). Host only; no context. */
+aqt_status aqt_observables_from_sums(int n_grid, int64_t M, const double *sum_x, const double *sum_x2,
+                                     double *mean, double *stderr_);
+
 /* Precision check of the frame rotation (its own arithmetic, as run): the
  * largest |(squared norm after a rotation c <- O c) / (before) - 1| over all
  * trajectories and grid steps of the last run. O is orthogonal, so this is
@@ -249,6 +256,63 @@ aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
 aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, double *final_states,
                                   aqt_jump *jumps, int64_t jump_capacity, unsigned long long *jump_count,
                                   int32_t *status);
+
+/* ---- Batches: many instances in one launch ------------------------------------
+ * Many independent annealing instances -- each its own context with its own
+ * Hamiltonian, grid, trajectories and precision, sizes N = 2 .. 1024 mixed --
+ * propagated together: the trajectories of different instances are as
+ * independent as those of one instance (Sec. VI.C), so a batch is a list of
+ * work items (instance, tile of trajectories) that one persistent kernel per
+ * kernel form takes from a queue, longest first. Forms: SIMT FP64, SIMT FP32
+ * (any N) and tensor cores (AQT_PREC_F16SPLIT, N = 128 or 256; one launch per
+ * N). One run is one CUDA graph launch (counters zeroed, the persistent
+ * kernels, the observable reductions). Results are those of aqt_run on each
+ * member: each member's outputs (observables, jumps, final states, status)
+ * are read with that member's getters after aqt_batch_sync.
+ *
+ * Tile shapes come from an autotuner: per kernel form it times the candidate
+ * shapes (SIMT: rotation rows per thread 2, 4, 8 with the trajectories per
+ * tile that follow; tensor cores: the largest tile and half of it) on the
+ * batch itself over its first 33 grid points, and keeps the fastest. The
+ * choice is cached for the process per (device, form, instance sizes), so a
+ * second batch of the same sizes is not timed again.
+ *
+ * Members: contexts on one device, each with its tables built on a bound
+ * workspace (aqt_build_tables); a context belongs to at most one batch at a
+ * time, and must not run on its own while the batch runs. Changing a member's
+ * inputs or workspace makes aqt_batch_run return AQT_EINVAL (create a new
+ * batch). The batch's own device memory (run parameters, work items,
+ * per-tile observable partials, jump scratch of the persistent CTAs) is one
+ * caller-owned workspace, as for a context. Not thread-safe. */
+typedef struct aqt_batch aqt_batch;
+
+/* members[n_members]: distinct contexts with device tables. Errors: AQT_EINVAL
+ * (no member, repeated member, members on different devices, tables not on
+ * the device), AQT_ECUDA. */
+aqt_status aqt_batch_create(aqt_batch **out, aqt_ctx *const *members, int n_members);
+void aqt_batch_destroy(aqt_batch *batch);
+const char *aqt_batch_last_error(const aqt_batch *batch);
+/* Device bytes of the batch's workspace (sized for every tuning candidate). */
+aqt_status aqt_batch_workspace_size(aqt_batch *batch, size_t *bytes);
+/* 256-byte-aligned caller-owned device memory of at least that size; it must
+ * outlive the batch or be rebound. */
+aqt_status aqt_batch_bind_workspace(aqt_batch *batch, void *dptr, size_t bytes);
+/* Run the autotuner now (otherwise the first aqt_batch_run does). Blocking:
+ * waits for `stream`, then times the candidates on an internal stream. The
+ * tuning runs write into the members' outputs, which the next run replaces. */
+aqt_status aqt_batch_tune(aqt_batch *batch, void *stream);
+/* One run of every member (asynchronous on `stream` after the first call,
+ * which tunes and builds the graph). Each call restarts every member from its
+ * initial state with the same random streams. */
+aqt_status aqt_batch_run(aqt_batch *batch, void *stream);
+/* Wait for the run; member_status[n_members] (may be NULL) gets each member's
+ * aqt_sync status. Returns AQT_OK, or the first member error (message names
+ * the member). */
+aqt_status aqt_batch_sync(aqt_batch *batch, int32_t *member_status);
+/* Shape the last run used for member i: shape[4] = (form: 0 SIMT FP64, 1 SIMT
+ * FP32, 2 tensor cores; trajectories per tile; rotation rows per thread
+ * (SIMT) or 128-level blocks (tensor cores); tiles). */
+aqt_status aqt_batch_get_shape(aqt_batch *batch, int member, int32_t *shape);
 
 /* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes

@@ -25,8 +25,10 @@ STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4
 EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
            "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
            "aqt_bind_workspace", "aqt_build_tables", "aqt_get_dt_bounds", "aqt_set_wait_limit", "aqt_run", "aqt_sync", "aqt_get_observables",
-           "aqt_get_observable_sums", "aqt_get_rotation_error", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
-           "aqt_run_static_scratch"]
+           "aqt_get_observable_sums", "aqt_observables_from_sums", "aqt_get_rotation_error", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
+           "aqt_run_static_scratch", "aqt_batch_create", "aqt_batch_destroy", "aqt_batch_last_error",
+           "aqt_batch_workspace_size", "aqt_batch_bind_workspace", "aqt_batch_tune", "aqt_batch_run", "aqt_batch_sync",
+           "aqt_batch_get_shape"]
 
 
 class aqt_jump(C.Structure):
@@ -73,11 +75,21 @@ def lib():
             "aqt_sync": (I, [P]),
             "aqt_get_observables": (I, [P, D, D]),
             "aqt_get_observable_sums": (I, [P, D, D]),
+            "aqt_observables_from_sums": (I, [I, I64, D, D, D, D]),
             "aqt_get_rotation_error": (I, [P, D]),
             "aqt_get_jumps": (I, [P, C.POINTER(aqt_jump), I64, C.POINTER(I64), C.POINTER(I64)]),
             "aqt_get_final_state": (I, [P, I, D]),
             "aqt_debug_table": (I, [P, I, I, D]),
             "aqt_run_static_scratch": (I, [P, P, P, P, P, I64, P, P]),
+            "aqt_batch_create": (I, [C.POINTER(P), C.POINTER(P), I]),
+            "aqt_batch_destroy": (None, [P]),
+            "aqt_batch_last_error": (C.c_char_p, [P]),
+            "aqt_batch_workspace_size": (I, [P, C.POINTER(SZ)]),
+            "aqt_batch_bind_workspace": (I, [P, P, SZ]),
+            "aqt_batch_tune": (I, [P, P]),
+            "aqt_batch_run": (I, [P, P]),
+            "aqt_batch_sync": (I, [P, C.POINTER(C.c_int32)]),
+            "aqt_batch_get_shape": (I, [P, I, C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -195,6 +207,15 @@ def aqt_get_observable_sums(ctx, n_grid: int):
     return s1, s2
 
 
+def aqt_observables_from_sums(M: int, sum_x, sum_x2):
+    s1, s2 = _f64(sum_x), _f64(sum_x2)
+    mean, se = np.empty(len(s1)), np.empty(len(s1))
+    st = lib().aqt_observables_from_sums(len(s1), int(M), _dp(s1), _dp(s2), _dp(mean), _dp(se))
+    if st != AQT_OK:
+        raise AqtError(st, "aqt_observables_from_sums")
+    return mean, se
+
+
 def aqt_get_rotation_error(ctx) -> float:
     v = C.c_double()
     _check(ctx, lib().aqt_get_rotation_error(ctx, C.byref(v)))
@@ -228,6 +249,62 @@ def aqt_run_static_scratch(ctx, stream: int, obs_sums: int, final_states: int, j
     _check(ctx, lib().aqt_run_static_scratch(ctx, C.c_void_p(stream), C.c_void_p(obs_sums),
                                              C.c_void_p(final_states), C.c_void_p(jumps), int(jump_capacity),
                                              C.c_void_p(jump_count), C.c_void_p(status)))
+
+
+def _bcheck(b, st):
+    if st != AQT_OK:
+        msg = lib().aqt_batch_last_error(b).decode() if b else ""
+        raise AqtError(st, msg)
+
+
+def aqt_batch_create(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    h = C.c_void_p()
+    st = lib().aqt_batch_create(C.byref(h), arr, len(ctxs))
+    if st != AQT_OK:
+        raise AqtError(st, "aqt_batch_create")
+    return h
+
+
+def aqt_batch_destroy(b):
+    lib().aqt_batch_destroy(b)
+
+
+def aqt_batch_last_error(b) -> str:
+    return lib().aqt_batch_last_error(b).decode()
+
+
+def aqt_batch_workspace_size(b) -> int:
+    n = C.c_size_t()
+    _bcheck(b, lib().aqt_batch_workspace_size(b, C.byref(n)))
+    return n.value
+
+
+def aqt_batch_bind_workspace(b, dptr: int, nbytes: int):
+    _bcheck(b, lib().aqt_batch_bind_workspace(b, C.c_void_p(dptr), nbytes))
+
+
+def aqt_batch_tune(b, stream: int = 0):
+    _bcheck(b, lib().aqt_batch_tune(b, C.c_void_p(stream)))
+
+
+def aqt_batch_run(b, stream: int = 0):
+    _bcheck(b, lib().aqt_batch_run(b, C.c_void_p(stream)))
+
+
+def aqt_batch_sync(b, n_members: int):
+    """Returns (status, per-member statuses); raises on errors other than AQT_EOVERFLOW."""
+    ms = (C.c_int32 * n_members)()
+    st = lib().aqt_batch_sync(b, ms)
+    if st not in (AQT_OK, AQT_EOVERFLOW):
+        _bcheck(b, st)
+    return st, [int(x) for x in ms]
+
+
+def aqt_batch_get_shape(b, member: int):
+    out = (C.c_int32 * 4)()
+    _bcheck(b, lib().aqt_batch_get_shape(b, int(member), out))
+    return tuple(int(x) for x in out)
 
 
 # ---- convenience ------------------------------------------------------------------

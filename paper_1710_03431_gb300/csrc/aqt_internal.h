@@ -190,6 +190,45 @@ inline size_t scratch_bytes(int n_cta, int N, int TT, bool tensor_core) {
 // Launch the propagation (precision per aqt_precision) and the observable
 // reduction on `stream`. Returns a CUDA error code (0 on success).
 int launch_run(const RunParams &p, int precision, void *stream, size_t smem_bytes);
+int launch_simt_f32(const RunParams &p, void *stream, size_t smem);
+int launch_simt_f64(const RunParams &p, void *stream, size_t smem);
+
+// ---------------------------------------------------------- batches ---------
+// One work item of a batched launch: tile `cta` (trajectories cta*TT ..) of
+// instance `inst`.
+struct BatchItem {
+    int32_t inst, cta;
+};
+
+// A persistent launch over the work items of many instances (device
+// pointers): params[inst] are the instances' run parameters, items the work
+// items in the order CTAs take them (queue: a counter that starts at 0),
+// scratch one jump-scratch block of scr_stride double2 per CTA of the launch.
+struct BatchLaunch {
+    const RunParams *params = nullptr;
+    const BatchItem *items = nullptr;
+    int n_items = 0;
+    int *queue = nullptr;
+    void *scratch = nullptr;
+    size_t scr_stride = 0;
+    int n_cta = 0;   // CTAs of the launch
+    int RA = 0;      // SIMT: rotation rows per thread (all instances of the launch)
+    int MH = 0;      // tensor cores: 128-level blocks (all instances of the launch)
+    size_t smem = 0; // dynamic shared memory per CTA
+    uint32_t tc_tail = 0;  // tensor cores: shared-memory offset of the per-CTA words
+    bool prepare_only = false;  // set the kernel's attributes only (before a stream capture)
+};
+int launch_simt_batch_f32(const BatchLaunch &b, void *stream);
+int launch_simt_batch_f64(const BatchLaunch &b, void *stream);
+int simt_batch_occupancy_f32(int RA, size_t smem);
+int simt_batch_occupancy_f64(int RA, size_t smem);
+int launch_tc_batch(const BatchLaunch &b, void *stream);
+size_t tc_batch_scratch_double2(int N, int TT_max);
+size_t tc_batch_smem_bytes(int N, int TT_max, uint32_t *tail);
+// Sum the observable partials of every instance of a batch (params on the device).
+int launch_reduce_batch(const RunParams *dev_params, int n_inst, int max_K, void *stream);
+int simt_rows_per_thread(int N, int TT);
+constexpr size_t kSimtSmemLimit = 200 * 1024;
 
 // Context accessors for the static-scratch run entry point (static_scratch.cu):
 // the scratch bytes a run of the current inputs needs, the run parameters
@@ -197,6 +236,20 @@ int launch_run(const RunParams &p, int precision, void *stream, size_t smem_byte
 // the precision and the kernel's dynamic shared memory.
 aqt_status static_scratch_need(aqt_ctx *ctx, size_t *bytes);
 aqt_status static_run_params(aqt_ctx *ctx, RunParams *p);
+
+// A context as a member of a batch: its run parameters over its device tables
+// and workspace outputs (obs_part and scratch are replaced by the batch's),
+// device, SM count, precision, and the version of its tables and workspace
+// (a batch refuses to run once a member's version has changed).
+struct BatchMember {
+    RunParams p;
+    int device = -1, num_sms = 0, precision = 0;
+    uint64_t version = 0;
+};
+aqt_status batch_member(aqt_ctx *ctx, BatchMember *m);
+uint64_t ctx_version(const aqt_ctx *ctx);
+// Let aqt_sync and the getters of the context read the batch's run on `stream`.
+void batch_member_ran(aqt_ctx *ctx, void *stream);
 aqt_status set_error(aqt_ctx *ctx, aqt_status st, const std::string &msg);
 int run_precision(const aqt_ctx *ctx);
 size_t run_smem(const aqt_ctx *ctx);

@@ -38,6 +38,7 @@ struct aqt_ctx {
     bool ran = false;
     long long wait_polls = kDefaultWaitPolls;
     size_t uploaded = 0;  // bytes copied to the device by the last aqt_build_tables
+    uint64_t version = 0;  // changes whenever the device tables or the workspace stop being valid
 };
 
 namespace {
@@ -57,6 +58,7 @@ bool inputs_complete(const aqt_ctx *c) {
 }
 
 void invalidate(aqt_ctx *c) {
+    ++c->version;
     c->tables_built = false;
     c->tables_on_device = false;
     c->ran = false;
@@ -125,11 +127,11 @@ void compute_layout(aqt_ctx *c) {
     L.total = off;
 }
 
-// Sizes the device paths take: the jump warp holds N/32 levels per lane in
-// registers (at most 8, so N <= 256); the tensor-core tiles take N = 128 or 256.
+// Sizes the device paths take: the SIMT kernels take N <= 1024 (the jump
+// warp holds N/32 levels per lane); the tensor-core tiles take N = 128 or 256.
 aqt_status device_shape_check(aqt_ctx *c) {
-    if (c->in.n > 8) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 8 (N <= 256)");
-    if (c->in.precision == AQT_PREC_F16SPLIT && c->in.n < 7)
+    if (c->in.n > 10) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 10 (N <= 1024)");
+    if (c->in.precision == AQT_PREC_F16SPLIT && (c->in.n < 7 || c->in.n > 8))
         return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
     if (c->in.precision == AQT_PREC_F16SPLIT && c->in.timing == AQT_JUMP_FIXED_STEP)
         return fail(c, AQT_EINVAL, "the fixed-step sampler runs on the SIMT paths (AQT_PREC_FP64, AQT_PREC_FP32)");
@@ -244,6 +246,26 @@ aqt_status static_scratch_need(aqt_ctx *c, size_t *bytes) {
     const size_t part = ((size_t)c->n_cta * K * 2 * 8 + 255) & ~(size_t)255;
     *bytes = part + scratch_bytes(c->n_cta, (int)N, c->TT, c->in.precision == AQT_PREC_F16SPLIT);
     return AQT_OK;
+}
+
+aqt_status batch_member(aqt_ctx *c, BatchMember *m) {
+    if (!c->tables_on_device) return fail(c, AQT_EINVAL, "build tables on the device before batching");
+    aqt_status s = device_shape_check(c);
+    if (s == AQT_OK) s = use_device(c);
+    if (s != AQT_OK) return s;
+    fill_params(c, &m->p);
+    m->device = c->device;
+    m->num_sms = c->num_sms;
+    m->precision = c->in.precision;
+    m->version = c->version;
+    return AQT_OK;
+}
+
+uint64_t ctx_version(const aqt_ctx *c) { return c->version; }
+
+void batch_member_ran(aqt_ctx *c, void *stream) {
+    c->stream = (cudaStream_t)stream;
+    c->ran = true;
 }
 
 aqt_status static_run_params(aqt_ctx *c, RunParams *p) {
@@ -388,6 +410,7 @@ aqt_status aqt_bind_workspace(aqt_ctx *c, void *dptr, size_t bytes) {
     if (bytes < c->lay.total) return fail(c, AQT_ENOMEM, "workspace smaller than aqt_workspace_size");
     c->ws = (unsigned char *)dptr;
     c->ws_bytes = bytes;
+    ++c->version;
     c->tables_on_device = false;
     c->ran = false;
     return AQT_OK;
@@ -589,20 +612,26 @@ aqt_status aqt_get_rotation_error(aqt_ctx *c, double *max_rel) {
     return AQT_OK;
 }
 
+aqt_status aqt_observables_from_sums(int n_grid, int64_t M, const double *sum_x, const double *sum_x2,
+                                     double *mean, double *stderr_) {
+    if (n_grid < 1 || M < 1 || !sum_x || !sum_x2 || !mean || !stderr_) return AQT_EINVAL;
+    const double R = (double)M;
+    for (int g = 0; g < n_grid; ++g) {
+        mean[g] = sum_x[g] / R;
+        // Eq. stderror: sigma^2 = sum (x - mean)^2 / (R (R - 1))
+        const double ss = std::max(0.0, sum_x2[g] - R * mean[g] * mean[g]);
+        stderr_[g] = R > 1 ? std::sqrt(ss / (R * (R - 1.0))) : 0.0;
+    }
+    return AQT_OK;
+}
+
 aqt_status aqt_get_observables(aqt_ctx *c, double *mean, double *stderr_) {
     if (!c || !mean || !stderr_) return AQT_EINVAL;
     const int K = c->in.K;
     std::vector<double> s1(K), s2(K);
     aqt_status s = aqt_get_observable_sums(c, s1.data(), s2.data());
     if (s != AQT_OK) return s;
-    const double R = (double)c->in.M;
-    for (int g = 0; g < K; ++g) {
-        mean[g] = s1[g] / R;
-        // Eq. stderror: sigma^2 = sum (x - mean)^2 / (R (R - 1))
-        const double ss = std::max(0.0, s2[g] - R * mean[g] * mean[g]);
-        stderr_[g] = R > 1 ? std::sqrt(ss / (R * (R - 1.0))) : 0.0;
-    }
-    return AQT_OK;
+    return aqt_observables_from_sums(K, c->in.M, s1.data(), s2.data(), mean, stderr_);
 }
 
 aqt_status aqt_get_jumps(aqt_ctx *c, aqt_jump *host_buf, int64_t cap, int64_t *n_out, int64_t *n_dropped) {

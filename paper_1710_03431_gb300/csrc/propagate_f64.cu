@@ -1,0 +1,11 @@
+// SIMT propagation kernel with a double state, one CTA per tile of one
+// instance; the tile body is in simt_kernel.cuh.
+#include "simt_kernel.cuh"
+
+namespace aqt {
+
+int launch_simt_f64(const RunParams &p, void *stream, size_t smem) {
+    return simt::launch_simt_ra<double>(p, (cudaStream_t)stream, smem);
+}
+
+}  // namespace aqt

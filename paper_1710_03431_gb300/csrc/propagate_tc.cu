@@ -359,9 +359,17 @@ __device__ __forceinline__ float2 rotate_row(const unsigned char *tile, const fl
     return make_float2(yr, yi);
 }
 
-template <int MH>  // 128-level blocks of the state (N = 128 MH)
-__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+// The whole run of tile `cta` of one instance (trajectories cta*TT .. cta*TT +
+// TT - 1). kBatch = false: the CTA owns its tensor memory here (one tile per
+// CTA). kBatch = true: the caller (a persistent CTA that runs tiles one after
+// another) holds 512 tensor-memory columns at tmem_batch; each tile
+// initialises its barriers and, at the end, makes sure every arrival on them
+// has landed and invalidates them, so that the next tile can initialise them
+// again. scr: this CTA's jump slots; patch: its next-step products of jumped
+// trajectories ([TT][N] float2).
+template <int MH, bool kBatch>  // 128-level blocks of the state (N = 128 MH)
+__device__ __forceinline__ bool tc_tile(const RunParams &p, int cta, unsigned char *smem, uint32_t tmem_batch,
+                                        double2 *scr, float2 *patch) {
     const int N = p.N, K = p.K, TT = p.TT, NC = 2 * TT, NK = N / 16, nchunk = NC / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t b_bytes = (size_t)N * NC * 2;
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     // b1lo: the products of block h = 1 no longer read the operand's first half
     // of levels (all products of block 0 are done too)
     const uint32_t bar_b1lo = bar_rowsB + 8;
-    const int64_t t0 = (int64_t)blockIdx.x * TT;
+    const int64_t t0 = (int64_t)cta * TT;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     const uint32_t park = (uint32_t)(MH * NC);
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(MH * NC + 12 * nchunk)) ncols <<= 1;
-    if (warp == 1) {
+    if (!kBatch && warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(S.tmem_base)),
                      "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *S.tmem_base;
+    const uint32_t tmem = kBatch ? tmem_batch : *S.tmem_base;
     const unsigned char *otab = reinterpret_cast<const unsigned char *>(p.tab.OT);
     const size_t tile = (size_t)N * N * 4;  // one step's rotation: FP16 hi + lo
 
@@ -434,7 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             // every CTA reads the same rotation tile in each step; each warms L2 with
             // its slice of the tile one step ahead, so the ring's copies hit L2
             const size_t piece = ((tile + p.n_cta - 1) / p.n_cta + 15) & ~(size_t)15;
-            const size_t poff = (size_t)blockIdx.x * piece;
+            const size_t poff = (size_t)cta * piece;
             auto warm = [&](int tg) {
                 if (tg < K - 1 && poff < tile)
                     l2_prefetch(otab + (size_t)tg * tile + poff, (uint32_t)(piece < tile - poff ? piece : tile - poff));
@@ -481,6 +489,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             const uint64_t dBh = umma_desc(bhi, b_lbo, b_sbo), dBl = umma_desc(blo, b_lbo, b_sbo);
             long long it = 0;
             uint32_t last_bar = 0, last_par = 0;
+            long long b1lo_commits = 0;
             bool run = true;
             for (int g = 1; g < K && run; ++g) {
                 for (int h = 0; h < MH && run; ++h)
@@ -514,13 +523,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                         umma_commit(bar_empty + 8 * slot);
                         last_bar = bar_empty + 8 * slot;
                         last_par = (uint32_t)((it / kStages) & 1);
-                        if (MH == 2 && h == 1 && kp == NK / 4 - 1) umma_commit(bar_b1lo);
+                        if (MH == 2 && h == 1 && kp == NK / 4 - 1) {
+                            umma_commit(bar_b1lo);
+                            ++b1lo_commits;
+                        }
                     }
                 if (run) umma_commit(bar_dfull);
             }
+            // between the tiles of a persistent CTA: every commit of the last ring
+            // round and of b1lo has arrived before the barriers are invalidated
+            if (kBatch) {
+                for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
+                    if (!mbar_drain(bar_empty + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), p.status,
+                                    kSiteAbort))
+                        break;
+                if (MH == 2 && b1lo_commits > 0)
+                    mbar_drain(bar_b1lo, (uint32_t)((b1lo_commits - 1) & 1), p.status, kSiteAbort);
+            }
             // on an abort, let the products already issued finish (bounded)
             // before the tensor memory is released
-            if (*S.abort_flag && last_bar) {
+            if (!kBatch && *S.abort_flag && last_bar) {
                 const unsigned long long ta = global_ns();
                 for (long long i = 0; i < kWaitLimit; ++i) {
                     if (mbar_try(last_bar, last_par)) break;
@@ -535,13 +557,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
         // ---------------- epilogue (warps 2..13) ----------------
         const int etid = tid - 64, e = etid >> 5, q = warp & 3, ch = e >> 2;  // ch: column group 0..2
         const int c_begin = (ch * nchunk) / 3, c_end = ((ch + 1) * nchunk) / 3;
-        // jump slots: general-jump scratch (2N double2), then the FP32 state planes
-        double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * kSlotDouble2 * N;
+        // jump slots (scr): general-jump scratch (2N double2), then the FP32 state planes
         auto slot_re = [&](int sidx) { return reinterpret_cast<float *>(scr + ((size_t)sidx * kSlotDouble2 + 2) * N); };
-        // next-step products of trajectories that jumped: [TT][N]
-        float2 *patch = reinterpret_cast<float2 *>(reinterpret_cast<double2 *>(p.scratch) +
-                                                   (size_t)p.n_cta * kSlots * kSlotDouble2 * N) +
-                        (size_t)blockIdx.x * TT * N;
+        // next-step products of trajectories that jumped: patch[TT][N]
         const float4 *lvl = reinterpret_cast<const float4 *>(p.tab.tclvl);
 
         // ---- initial state e_0 and the half-step after s_0 ------------------------
@@ -635,8 +653,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
             }
             warp_sum2(sx, sx2);
             if (lane == 0) {
-                p.obs_part[((size_t)blockIdx.x * K) * 2] = sx;
-                p.obs_part[((size_t)blockIdx.x * K) * 2 + 1] = sx2;
+                p.obs_part[((size_t)cta * K) * 2] = sx;
+                p.obs_part[((size_t)cta * K) * 2 + 1] = sx2;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1050,8 +1068,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
                 }
                 warp_sum2(sx, sx2);
                 if (lane == 0) {
-                    p.obs_part[((size_t)blockIdx.x * K + g) * 2] = sx;
-                    p.obs_part[((size_t)blockIdx.x * K + g) * 2 + 1] = sx2;
+                    p.obs_part[((size_t)cta * K + g) * 2] = sx;
+                    p.obs_part[((size_t)cta * K + g) * 2 + 1] = sx2;
                 }
             }
         }
@@ -1060,7 +1078,73 @@ __global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    if (!kBatch && warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    const bool completed = *S.abort_flag == 0;
+    if (kBatch && tid == 0 && completed) {
+        // every arrival has landed (the roles waited for their last phases above)
+        for (int i = 0; i < 2 * kStages + 4; ++i)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar_full + 8 * i) : "memory");
+    }
+    return completed;
+}
+
+// One CTA per tile of one instance.
+template <int MH>
+__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * kSlotDouble2 * p.N;
+    float2 *patch = reinterpret_cast<float2 *>(reinterpret_cast<double2 *>(p.scratch) +
+                                               (size_t)p.n_cta * kSlots * kSlotDouble2 * p.N) +
+                    (size_t)blockIdx.x * p.TT * p.N;
+    tc_tile<MH, false>(p, blockIdx.x, smem, 0u, scr, patch);
+}
+
+// Persistent kernel over the work items of many instances with the same N
+// (one CTA per SM): the CTA holds 512 tensor-memory columns for its whole
+// life and runs the tiles it takes from the queue one after another. Its own
+// scratch block (scr_stride double2): the jump slots, then the patch buffer
+// of the largest tile. tail: byte offset of three words past the largest
+// tile's shared memory (item index, tensor-memory base, and the run
+// parameters after them).
+template <int MH>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    propagate_tc_batch(const RunParams *ps, const BatchItem *items, int n_items, int *queue, double2 *scratch,
+                       size_t scr_stride, uint32_t tail) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    int *s_item = reinterpret_cast<int *>(smem + tail);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + tail + 16);
+    RunParams *sp = reinterpret_cast<RunParams *>(smem + tail + 64);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *s_tmem;
+    double2 *scr = scratch + (size_t)blockIdx.x * scr_stride;
+    for (;;) {
+        __syncthreads();  // the previous tile is done with the shared memory
+        if (threadIdx.x == 0) {
+            *s_item = atomicAdd(queue, 1);
+            if (*s_item < n_items) *sp = ps[items[*s_item].inst];
+        }
+        __syncthreads();
+        const int it = *s_item;
+        if (it >= n_items) break;
+        float2 *patch = reinterpret_cast<float2 *>(scr + (size_t)kSlots * kSlotDouble2 * sp->N);
+        // after an abort (a bounded wait expired; the instance reports
+        // AQT_ETIMEOUT) commits may still be landing on this tile's barriers, so
+        // the CTA takes no further tile
+        if (!tc_tile<MH, true>(*sp, items[it].cta, smem, tmem, scr, patch)) break;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 }  // namespace
@@ -1084,6 +1168,32 @@ int tc_shape(int N, int64_t M, int num_sms) {
     // shared memory, and tensor-memory columns: products plus parked sums (12 per 8 columns)
     while (tt > 8 && (tc_smem_bytes(N, tt) > 227 * 1024 || 2 * tt * (N / 128) + 3 * tt > 512 || 2 * tt > 256)) tt -= 8;
     return tt;
+}
+
+// Scratch of one persistent CTA of a batch (double2): jump slots and the
+// patch buffer of the largest tile.
+size_t tc_batch_scratch_double2(int N, int TT_max) {
+    return (size_t)kSlots * kSlotDouble2 * N + ((size_t)TT_max * N + 1) / 2;
+}
+
+// Shared memory of a persistent batch CTA: the largest tile's, then the tail
+// (item index, tensor-memory base, run parameters).
+size_t tc_batch_smem_bytes(int N, int TT_max, uint32_t *tail) {
+    const size_t base = tc_smem_bytes(N, TT_max);
+    *tail = (uint32_t)base;
+    return base + 64 + ((sizeof(RunParams) + 15) & ~(size_t)15);
+}
+
+int launch_tc_batch(const BatchLaunch &b, void *stream) {
+    auto kern = b.MH == 1 ? propagate_tc_batch<1> : b.MH == 2 ? propagate_tc_batch<2> : nullptr;
+    if (!kern) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem);
+    if (e != cudaSuccess) return (int)e;
+    if (b.prepare_only) return 0;
+    kern<<<b.n_cta, kTcThreads, b.smem, (cudaStream_t)stream>>>(b.params, b.items, b.n_items, b.queue,
+                                                                 reinterpret_cast<double2 *>(b.scratch), b.scr_stride,
+                                                                 b.tc_tail);
+    return (int)cudaGetLastError();
 }
 
 int launch_tc(const RunParams &p, void *stream, size_t smem) {

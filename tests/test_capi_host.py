@@ -141,13 +141,32 @@ def test_grid_metadata_matches_oracle(aqt_lib, n, seed, grid, idx):
     A.aqt_destroy(c)
 
 
-def test_device_runs_limited_to_256_levels(aqt_lib):
+def test_device_run_sizes(aqt_lib):
+    """SIMT runs take up to 1024 levels (n = 10); the tensor-core path only
+    N = 128 or 256."""
     A = aqt_lib
     inst = W.tfim_instance(9, 3, n_grid=3)
-    c = _host_ctx(A, inst)
+    c = _host_ctx(A, inst, precision=A.AQT_PREC_FP32)
+    assert A.aqt_workspace_size(c) > 2 * 512 * 512 * 4  # eigenvectors and rotations of 3 grid points
+    A.aqt_destroy(c)
+    c = _host_ctx(A, inst, precision=A.AQT_PREC_F16SPLIT)
     with pytest.raises(A.AqtError) as e:
         A.aqt_workspace_size(c)
     assert e.value.status == A.AQT_EINVAL
+    A.aqt_destroy(c)
+
+
+def test_batch_needs_device_tables(aqt_lib):
+    """A batch takes contexts whose tables are on a device; a host-only
+    context (or none) is refused."""
+    A = aqt_lib
+    inst = W.tfim_instance(3, 5, n_grid=5)
+    c = _host_ctx(A, inst)
+    A.aqt_build_tables(c)
+    for members in ([c], []):
+        with pytest.raises(A.AqtError) as e:
+            A.aqt_batch_create(members)
+        assert e.value.status == A.AQT_EINVAL
     A.aqt_destroy(c)
 
 

@@ -139,3 +139,19 @@ def case0989_instance(**kw) -> Instance:
         J[i, j] = v / 3.0
     s, A, B = linear_schedule()
     return Instance(n_qubits=8, hz=-h, J=J, sched_s=s, sched_A=A, sched_B=B, **kw)
+
+
+def cfg_batch(n_instances: int = 64, qubits=(6, 7, 8), M: int = 2048, n_grid: int = 1000, t_f: float = 20.0,
+              **kw):
+    """Batch of independent instances of uneven size: instance i has
+    qubits[i % len(qubits)] qubits and its own seeded couplings (instance seed
+    1710_03500 + i) and trajectory streams, t_f = 20 ns, 1000-point grid,
+    M = 2048 trajectories each."""
+    out = []
+    for i in range(n_instances):
+        n = qubits[i % len(qubits)]
+        base = dict(t_f=t_f, n_grid=n_grid, M=M, seed=1710_03500 + 7919 * i)
+        base.update(kw)
+        out.append(tfim_instance(n, 1710_03500 + i, **base))
+    return out
+
