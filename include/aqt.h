@@ -140,8 +140,9 @@ aqt_status aqt_set_trajectories(aqt_ctx *ctx, int64_t M, uint64_t seed, int prec
                                 int64_t jump_capacity);
 
 /* Device bytes the caller must provide for the current inputs. Device runs
- * take n_qubits <= 10 (N <= 1024; the jump warp keeps N/32 levels per lane)
- * and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise AQT_EINVAL. The size depends on
+ * take n_qubits <= 9 (N <= 512; the jump warp keeps N/32 levels per lane in
+ * registers) and, for AQT_PREC_F16SPLIT, n_qubits 7 or 8; otherwise
+ * AQT_EINVAL (host-only contexts build tables up to n_qubits = 10). The size depends on
  * the spectrum (full jump amplitudes are kept for the grid points with
  * degenerate levels or coinciding Bohr frequencies), so this call builds the
  * host tables of aqt_build_tables if they are not built yet, and can return
@@ -259,7 +260,7 @@ aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double *obs_sums, 
 
 /* ---- Batches: many instances in one launch ------------------------------------
  * Many independent annealing instances -- each its own context with its own
- * Hamiltonian, grid, trajectories and precision, sizes N = 2 .. 1024 mixed --
+ * Hamiltonian, grid, trajectories and precision, sizes N = 2 .. 512 mixed --
  * propagated together: the trajectories of different instances are as
  * independent as those of one instance (Sec. VI.C), so a batch is a list of
  * work items (instance, tile of trajectories) that one persistent kernel per

@@ -1,5 +1,5 @@
 // Batches: many independent annealing instances (each its own context, tables
-// and trajectories, sizes N = 2 .. 1024 mixed) propagated by one persistent
+// and trajectories, sizes N = 2 .. 512 mixed) propagated by one persistent
 // launch per kernel form, replayed as one CUDA graph.
 //
 // The trajectories of every instance are independent (arXiv:1710.03431,

@@ -127,10 +127,11 @@ void compute_layout(aqt_ctx *c) {
     L.total = off;
 }
 
-// Sizes the device paths take: the SIMT kernels take N <= 1024 (the jump
-// warp holds N/32 levels per lane); the tensor-core tiles take N = 128 or 256.
+// Sizes the device paths take: the SIMT kernels take N <= 512 (the jump
+// warp holds N/32 levels per lane in registers, at most 16); the tensor-core
+// tiles take N = 128 or 256.
 aqt_status device_shape_check(aqt_ctx *c) {
-    if (c->in.n > 10) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 10 (N <= 1024)");
+    if (c->in.n > 9) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 9 (N <= 512)");
     if (c->in.precision == AQT_PREC_F16SPLIT && (c->in.n < 7 || c->in.n > 8))
         return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
     if (c->in.precision == AQT_PREC_F16SPLIT && c->in.timing == AQT_JUMP_FIXED_STEP)

@@ -45,11 +45,6 @@ namespace aqt {
 namespace dev {
 
 constexpr int kMaxJumpsPerHalf = 64;
-// Unrolling of the loops over a lane's levels: full up to 8 levels per lane
-// (N <= 256: the state stays in registers); above that the loops stay loops
-// and the level arrays live in local memory, which only the rare jumps touch.
-template <int NPL>
-constexpr int kUJ = NPL <= 8 ? NPL : 1;
 constexpr int kMaxAlpha = 10;
 enum : int32_t { kStatusNumeric = 2, kStatusTimeout = 4 };
 
@@ -86,7 +81,7 @@ static __device__ __forceinline__ void m_sincos(double x, double *s, double *c) 
 template <typename T, int NPL>
 static __device__ __forceinline__ T reg_at(const T (&v)[NPL], int j) {
     T r = v[0];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int i = 1; i < NPL; ++i)
         if (i == j) r = v[i];
     return r;
@@ -99,15 +94,15 @@ static __device__ __forceinline__ T reg_at(const T (&v)[NPL], int j) {
 template <typename T, int NPL>
 static __device__ __forceinline__ int reg_pick(const T (&w)[NPL], T target, int lane) {
     T tot[NPL];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) tot[j] = w[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) tot[j] += __shfl_xor_sync(0xffffffffu, tot[j], o);
     T cum = T(0);
     int jsel = -1;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j)
         if (jsel < 0) {
             if (tot[j] > T(0) && cum + tot[j] > target) jsel = j;
@@ -125,7 +120,7 @@ static __device__ __forceinline__ int reg_pick(const T (&w)[NPL], T target, int 
         if (hit) return 32 * jsel + __ffs(hit) - 1;
     }
     int last = -1;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) {
         const unsigned pos = __ballot_sync(0xffffffffu, w[j] > T(0));
         if (pos) last = 32 * j + 31 - __clz(pos);
@@ -350,7 +345,7 @@ template <typename T, int NPL>
 static __device__ __forceinline__ void m_column(const RunParams &p, int g, int al, int b, int lane, T (&m)[NPL]) {
     const int N = p.N;
     const T *Vg = static_cast<const T *>(p.tab.V) + (size_t)g * N * N;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) m[j] = T(0);
     const int lo_mask = (1 << al) - 1;
 #pragma unroll 8
@@ -358,13 +353,13 @@ static __device__ __forceinline__ void m_column(const RunParams &p, int g, int a
         const int x = ((i >> al) << (al + 1)) | (1 << al) | (i & lo_mask);
         const T *row = Vg + (size_t)x * N;
         const T vb = row[b];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const int a = 32 * j + lane;
             if (a < N) m[j] = fma(row[a], vb, m[j]);
         }
     }
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) m[j] = (32 * j + lane == b ? T(1) : T(0)) - T(2) * m[j];
 }
 
@@ -389,7 +384,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
     int al = -1, bsrc = -1, adst = -1;
     if (fast) {
         double qv[NPL];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) qv[j] = pop(j);
         // stage one over units (alpha, b) in that order. The total rate is
         // sum_b |c_b|^2 sum_alpha G_alpha[b] = -sum_b |c_b|^2 2 Im K_bb, so the
@@ -397,13 +392,13 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
         // the target, one warp sum per alpha visited.
         double total = 0.0, cum = 0.0, cum_last = 0.0;
         int last = -1;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) total -= qv[j] * kim2d(j);
         total = warp_sum(total);
         const double target = u1 * total;
         for (int a_ = 0; a_ < n && al < 0; ++a_) {
             double acc = 0.0;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
             for (int j = 0; j < NPL; ++j) {
                 const int b = 32 * j + lane;
                 if (b < N) acc += qv[j] * Gg[(size_t)a_ * N + b];
@@ -422,7 +417,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
         }
         if (al >= 0) {
             double w[NPL];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
             for (int j = 0; j < NPL; ++j) {
                 const int b = 32 * j + lane;
                 w[j] = b < N ? qv[j] * Gg[(size_t)al * N + b] : 0.0;
@@ -436,7 +431,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
             double w[NPL], tot2 = 0.0;
             if (bsrc < p.n_low) {
                 const T *row = static_cast<const T *>(p.tab.Rlow) + (((size_t)g * n + al) * p.n_low + bsrc) * N;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int a = 32 * j + lane;
                     m[j] = a < N ? row[a] : T(0);
@@ -447,7 +442,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
                 m_column<T, NPL>(p, g, al, bsrc, lane, m);
                 const double *lvlE = p.tab.lvlE + (size_t)g * N;
                 const double eb = lvlE[bsrc];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int a = 32 * j + lane;
                     w[j] = a < N ? (double)bath_gamma(p, (T)(eb - lvlE[a])) * ((double)m[j] * (double)m[j]) : 0.0;
@@ -465,7 +460,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
                 const T m2 = br * br + bi * bi;
                 if (m2 > T(0)) {
                     const T f = (ra < T(0) ? T(-1) : T(1)) * m_rsqrt(m2);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
                     for (int j = 0; j < NPL; ++j) {
                         const bool hit = 32 * j + lane == adst;
                         cr[j] = hit ? br * f : T(0);
@@ -478,7 +473,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
                 // zero frequency: every level pairs with itself, y_a = sqrt(gamma(0)) M_alpha[a][a] c_a
                 const double *Md = p.tab.Mdiag + ((size_t)g * n + al) * N;
                 T s = T(0);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
                 for (int j = 0; j < NPL; ++j) {
                     const int a = 32 * j + lane;
                     const T d = a < N ? (T)Md[a] : T(0);
@@ -489,7 +484,7 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
                 s = warp_sum(s);
                 if (s > T(0)) {
                     const T inv = m_rsqrt(s);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
                     for (int j = 0; j < NPL; ++j) {
                         cr[j] *= inv;
                         ci[j] *= inv;
@@ -501,14 +496,14 @@ static __device__ __forceinline__ int draw_apply(const RunParams &p, int g, T (&
         }
         if (bsrc < 0 || adst < 0) al = -1;
     } else {
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const int a = 32 * j + lane;
             if (a < N) slow[a] = make_double2((double)cr[j], (double)ci[j]);
         }
         __syncwarp();
         al = general_draw_apply(p, g, u1, u2, slow, slow + N, lane, &bsrc, &adst);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const int a = 32 * j + lane;
             if (a < N) {
@@ -561,7 +556,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     const int N = p.N;
     const double *kd = p.tab.kdiag + (size_t)g * N * 2;
     T cr[NPL], ci[NPL];
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) {
         const int a = 32 * j + lane;
         const bool v = a < N;
@@ -592,7 +587,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     // c <- c exp(-i K t) / |.|; false if the norm is not positive and finite
     auto advance = [&](T t) -> bool {
         T s = T(0);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             T sn, cs;
             m_sincos(kre(j) * t, &sn, &cs);
@@ -605,7 +600,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         s = warp_sum(s);
         if (!(s > T(0)) || !isfinite(s)) return false;
         const T inv = m_rsqrt(s);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             cr[j] *= inv;
             ci[j] *= inv;
@@ -615,7 +610,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     // delta(t) of the normalised state and its derivative, FP64
     auto decay64 = [&](double t, double *d1) -> double {
         double d = 0.0, e1 = 0.0;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const double q = pop(j), x = kim2d(j);
             const double e = expm1_small(x * t);
@@ -629,7 +624,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     // the same in single precision (a cheap start for the root of float states)
     auto decay32 = [&](float t, float *d1) -> float {
         float d = 0.0f, e1 = 0.0f;
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const float q = (float)(cr[j] * cr[j] + ci[j] * ci[j]);
             const float x = (float)kim2(j);
@@ -735,7 +730,7 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
     if (!ok && lane == 0) atomicOr(p.status, kStatusNumeric);
     // finish the half-step without further jumps
     advance((T)tau_rem);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) {
         const int a = 32 * j + lane;
         if (a < N) {
@@ -758,7 +753,7 @@ static __device__ __forceinline__ void fixed_step_jump(const RunParams &p, int g
     const int N = p.N;
     T cr[NPL], ci[NPL];
     T s = T(0);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
     for (int j = 0; j < NPL; ++j) {
         const int a = 32 * j + lane;
         const bool v = a < N;
@@ -770,7 +765,7 @@ static __device__ __forceinline__ void fixed_step_jump(const RunParams &p, int g
     int al = -1, bsrc = -1, adst = -1;
     if (s > T(0) && isfinite(s)) {
         const T inv = m_rsqrt(s);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             cr[j] *= inv;
             ci[j] *= inv;
@@ -781,7 +776,7 @@ static __device__ __forceinline__ void fixed_step_jump(const RunParams &p, int g
         if (lane == 0) atomicOr(p.status, kStatusNumeric);
     } else {
         record_jump(p, traj, g, half, al, bsrc, adst, half == 0 ? g * p.dt - p.tau : g * p.dt, lane);
-#pragma unroll (kUJ<NPL>)
+#pragma unroll
         for (int j = 0; j < NPL; ++j) {
             const int a = 32 * j + lane;
             if (a < N) {
@@ -835,12 +830,10 @@ static __device__ __forceinline__ void fixed_step_jump_any(const RunParams &p, i
     else if (N <= 64) fixed_step_jump_ool<T, 2>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
     else if (N <= 128) fixed_step_jump_ool<T, 4>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
     else if (N <= 256) fixed_step_jump_ool<T, 8>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
-    else if (N <= 512) fixed_step_jump_ool<T, 16>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
-    else fixed_step_jump_ool<T, 32>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
+    else fixed_step_jump_ool<T, 16>(p, g, half, traj, sre, sim, stride, u1, u2, lane, slow);
 }
 
-// Register tile from N for the SIMT kernels (N <= 1024; above 256 levels the
-// tile spills to local memory, which only the rare jumps pay for).
+// Register tile from N for the SIMT kernels (N <= 512).
 template <typename T>
 static __device__ __forceinline__ void jump_half_step_any(const RunParams &p, int g, int half, int64_t traj, T *sre,
                                                           T *sim, int stride, double *ell, double *logr, int *nj,
@@ -850,8 +843,7 @@ static __device__ __forceinline__ void jump_half_step_any(const RunParams &p, in
     else if (N <= 64) jump_half_step_ool<T, 2>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
     else if (N <= 128) jump_half_step_ool<T, 4>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
     else if (N <= 256) jump_half_step_ool<T, 8>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
-    else if (N <= 512) jump_half_step_ool<T, 16>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
-    else jump_half_step_ool<T, 32>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
+    else jump_half_step_ool<T, 16>(p, g, half, traj, sre, sim, stride, ell, logr, nj, lane, slow);
 }
 
 }  // namespace dev

@@ -1091,7 +1091,7 @@ __device__ __forceinline__ bool tc_tile(const RunParams &p, int cta, unsigned ch
 
 // One CTA per tile of one instance.
 template <int MH>
-__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(RunParams p) {
+__global__ void __launch_bounds__(kTcThreads, 1) propagate_tc(const __grid_constant__ RunParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kSlots * kSlotDouble2 * p.N;
     float2 *patch = reinterpret_cast<float2 *>(reinterpret_cast<double2 *>(p.scratch) +

@@ -291,7 +291,7 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
 
 // One CTA per tile of one instance.
 template <typename R, int RA>
-__global__ void __launch_bounds__(kThreads, 2) propagate_simt(RunParams p) {
+__global__ void __launch_bounds__(kThreads, 2) propagate_simt(const __grid_constant__ RunParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     double2 *scr = reinterpret_cast<double2 *>(p.scratch) + (size_t)blockIdx.x * kScratchSlots * kSlotDouble2 * p.N;
     simt_tile<R, RA>(p, blockIdx.x, scr, smem);

@@ -142,7 +142,7 @@ def test_grid_metadata_matches_oracle(aqt_lib, n, seed, grid, idx):
 
 
 def test_device_run_sizes(aqt_lib):
-    """SIMT runs take up to 1024 levels (n = 10); the tensor-core path only
+    """SIMT runs take up to 512 levels (n = 9); the tensor-core path only
     N = 128 or 256."""
     A = aqt_lib
     inst = W.tfim_instance(9, 3, n_grid=3)
