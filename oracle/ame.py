@@ -14,6 +14,12 @@ The state starts in the ground state of H_S(0) (Sec. V.A). Observable: the
 population of the lowest degenerate manifold of H_S(s_k), recorded after the
 second half-step into s_k.
 
+Truncated model (``inst.n_levels``: the lowest levels only, a reading of the
+paper's 16-qubit use; the paper does not discuss truncation): the frame
+change O = V_k^T V_{k-1} is then not orthogonal; the weight it moves out of
+the kept levels (the leakage, 1 - tr(O rho O^T)) is recorded and renormalised
+away, never counted as jump probability.
+
 ``run_continuous`` integrates the same AME without the grid (Sec. II, Eqs.
 ME2-H, ME2-L): the generator is rebuilt from the eigensystem of H_S(s(t)) at
 every time the adaptive integrator asks for (Dormand-Prince 8(5,3)), which
@@ -62,6 +68,7 @@ def run(inst, closed_form: bool = True, keep_states: bool = False):
     s_grid, dt = model.grid(inst)
     tau = 0.5 * dt
     p_gs = np.empty(len(s_grid))
+    leak = np.zeros(len(s_grid))
     states = [] if keep_states else None
     prev = None
     rho = None
@@ -72,14 +79,19 @@ def run(inst, closed_form: bool = True, keep_states: bool = False):
         else:
             rho = half_step(prev, rho, tau, closed_form)           # frozen at s_{k-1}
             O = fr.eig.V.T @ prev.eig.V                          # frame s_{k-1} -> s_k
+            tr0 = np.trace(rho).real
             rho = O @ rho @ O.T
+            if fr.eig.truncated:
+                tr1 = np.trace(rho).real
+                leak[k] = 1.0 - tr1 / tr0
+                rho = rho * (tr0 / tr1)
             rho = half_step(fr, rho, tau, closed_form)             # frozen at s_k
         g0 = fr.eig.manifolds[0]
         p_gs[k] = float(np.real(np.trace(rho[np.ix_(g0, g0)])))
         if keep_states:
             states.append(rho.copy())
         prev = fr
-    out = {"s": s_grid, "p_gs": p_gs, "rho_final": rho}
+    out = {"s": s_grid, "p_gs": p_gs, "rho_final": rho, "leak": leak}
     if keep_states:
         out["states"] = states
     return out

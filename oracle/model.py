@@ -71,12 +71,23 @@ def energy_tol(evals: np.ndarray) -> float:
 
 
 class Eigen:
-    """Instantaneous eigensystem of H_S(s) with its degenerate manifolds."""
+    """Instantaneous eigensystem of H_S(s) with its degenerate manifolds.
 
-    def __init__(self, H: np.ndarray):
+    keep > 0 keeps only the lowest ``keep`` levels (a truncated model: the
+    system's Hilbert space is the span of those eigenstates at every s). The
+    cut must fall between manifolds: a level just above the cut within the
+    tolerance of the level just below it raises ValueError. The tolerance is
+    that of the kept levels."""
+
+    def __init__(self, H: np.ndarray, keep: int = 0):
         evals, V = np.linalg.eigh(H)
+        if 0 < keep < len(evals):
+            if evals[keep] - evals[keep - 1] <= energy_tol(evals[:keep]):
+                raise ValueError(f"keeping {keep} levels splits a degenerate manifold")
+            evals, V = evals[:keep], V[:, :keep]
         self.evals = evals
         self.V = V
+        self.truncated = V.shape[0] != V.shape[1]
         self.tol = energy_tol(evals)
         groups = [[0]]
         for a in range(1, len(evals)):
@@ -99,9 +110,10 @@ class Eigen:
 
 
 def eigen_at(inst, s: float, terms=None) -> Eigen:
+    """Eigensystem of H_S(s), truncated to inst.n_levels levels when set."""
     HX, HZ = terms if terms is not None else hamiltonian_terms(inst)
     A, B = schedule(inst, s)
-    return Eigen(A * HX + B * HZ)
+    return Eigen(A * HX + B * HZ, keep=getattr(inst, "n_levels", 0))
 
 
 def bohr_classes(eig: Eigen):

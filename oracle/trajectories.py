@@ -31,7 +31,12 @@ Readings shared with the CUDA path:
   * a jump record names the source and target manifolds by their lowest
     level: inside a degenerate manifold the level that stage two lands on
     depends on the arbitrary eigenbasis, the manifold (hence the channel and
-    the new state) does not.
+    the new state) does not;
+  * truncated model (``inst.n_levels``): the state stays in the span of the
+    kept eigenstates; at each grid change it is projected onto the new span
+    and rescaled to its norm before the projection, so the weight that leaves
+    the kept levels (the leakage) is renormalised away and never counted as
+    jump probability (the norm clock is untouched).
 """
 from __future__ import annotations
 
@@ -100,6 +105,15 @@ class Trajectory:
         self.n_jumps = 0
         self.jumps = []
 
+    def project(self, V: np.ndarray) -> float:
+        """Project onto the span of V's columns, keeping the norm; returns the
+        leaked fraction of the squared norm."""
+        n2 = np.vdot(self.psi, self.psi).real
+        new = V @ (V.T @ self.psi)
+        m2 = np.vdot(new, new).real
+        self.psi = new * np.sqrt(n2 / m2)
+        return 1.0 - m2 / n2
+
     def advance(self, piece: Piece, tau: float, t0: float, grid_index: int, half: int, timing: str = "refined"):
         """Propagate through one frozen piece of length tau starting at t0."""
         psi = self.psi
@@ -141,18 +155,21 @@ class Trajectory:
                 return
 
 
-def sample(inst, traj_ids, seed=None, timing: str = "refined"):
+def sample(inst, traj_ids, seed=None, timing: str = "refined", return_leak: bool = False):
     """Run the given trajectories over the whole grid (``timing``: "refined" or
     "grid", see the module docstring).
 
     Returns (p_gs [len(traj_ids), K], jumps (list of dicts), final psi
-    [len(traj_ids), N] in the computational basis, normalised).
+    [len(traj_ids), N] in the computational basis, normalised), and with
+    ``return_leak`` the leaked fraction at each frame change
+    [len(traj_ids), K] (zero without truncation).
     """
     seed = inst.seed if seed is None else seed
     s_grid, dt = model.grid(inst)
     tau = 0.5 * dt
     K = len(s_grid)
     p = np.empty((len(traj_ids), K))
+    leak = np.zeros((len(traj_ids), K))
     trajs = None
     prev = None
     for k, fr in enumerate(ame.frames(inst)):
@@ -162,8 +179,10 @@ def sample(inst, traj_ids, seed=None, timing: str = "refined"):
             trajs = [Trajectory(int(t), seed, psi0) for t in traj_ids]
         else:
             t_prev = (k - 1) * dt
-            for tr in trajs:
+            for i, tr in enumerate(trajs):
                 tr.advance(prev, tau, t_prev, k - 1, 1, timing)
+                if fr.eig.truncated:
+                    leak[i, k] = tr.project(fr.eig.V)
                 tr.advance(piece, tau, t_prev + tau, k, 0, timing)
         g0 = fr.eig.manifolds[0]
         for i, tr in enumerate(trajs):
@@ -172,6 +191,8 @@ def sample(inst, traj_ids, seed=None, timing: str = "refined"):
         prev = piece
     jumps = [j for tr in trajs for j in tr.jumps]
     final = np.array([tr.psi / np.linalg.norm(tr.psi) for tr in trajs])
+    if return_leak:
+        return p, jumps, final, leak
     return p, jumps, final
 
 
@@ -215,6 +236,9 @@ def sample_fixed_step(inst, traj_ids, seed=None):
             t_prev = (k - 1) * dt
             for i, tr in enumerate(traj_ids):
                 psis[i] = step(prev, psis[i], int(tr), 2 * k - 2, t_prev, k - 1, 1)
+                if fr.eig.truncated:  # frame change onto the kept levels, renormalised
+                    v = fr.eig.V @ (fr.eig.V.T @ psis[i])
+                    psis[i] = v / np.linalg.norm(v)
                 psis[i] = step(piece, psis[i], int(tr), 2 * k - 1, t_prev + tau, k, 0)
         g0 = fr.eig.manifolds[0]
         for i in range(len(traj_ids)):

@@ -551,3 +551,61 @@ def test_fixed_step_average_matches_density_matrix():
         mean = p[:, k].mean()
         se = max(p[:, k].std(ddof=1) / math.sqrt(M), math.sqrt(ref[k] * (1 - ref[k]) / M))
         assert abs(mean - ref[k]) < 3.5 * se, (k, mean, ref[k], se)
+
+
+# --- Truncated model (lowest levels only; a reading for the 16-qubit use) ------------------
+def test_truncation_cut_follows_s0_multiplicities():
+    """At s = 0 the levels of -A sum sx have multiplicities C(n, k): a cut is
+    allowed only at the cumulative sums 1, 1 + n, 1 + n + C(n, 2), ..."""
+    inst = W.tfim_instance(3, 5, n_grid=3)
+    allowed = set(np.cumsum([math.comb(3, k) for k in range(4)]).tolist())  # {1, 4, 7, 8}
+    for keep in range(1, 9):
+        inst.n_levels = keep
+        if keep in allowed:
+            eig = model.eigen_at(inst, 0.0)
+            assert eig.V.shape == (8, keep) and eig.truncated == (keep < 8)
+        else:
+            with pytest.raises(ValueError):
+                model.eigen_at(inst, 0.0)
+
+
+def test_truncated_first_frame_change_leaks_the_dropped_weight():
+    """No bath: the first frame change of the truncated sampler moves out of the
+    kept levels exactly the weight of the new frame's dropped levels in the
+    initial ground state, computed here from the full eigensystems."""
+    n, keep = 3, 4
+    inst = W.tfim_instance(n, 7, eta_g2=0.0, t_f=4.0, n_grid=3, seed=1, n_levels=keep)
+    _, jumps, _, leak = trajectories.sample(inst, [0, 1], return_leak=True)
+    assert not jumps
+    HX, HZ = model.hamiltonian_terms(inst)
+    e0, V0 = np.linalg.eigh(2 * math.pi * HX)                       # s = 0
+    e1, V1 = np.linalg.eigh(2 * math.pi * (0.5 * HX + 0.5 * HZ))    # s = 1/2
+    want = float(np.sum((V1[:, keep:].T @ V0[:, 0]) ** 2))
+    assert want > 1e-6
+    np.testing.assert_allclose(leak[:, 1], want, rtol=1e-10)
+
+
+def test_truncation_keeping_every_level_is_the_full_model():
+    inst = W.tfim_instance(2, 28, eta_g2=0.03, t_f=3.0, n_grid=21, seed=9)
+    full = ame.run(inst)
+    inst.n_levels = 4
+    same = ame.run(inst)
+    np.testing.assert_array_equal(full["p_gs"], same["p_gs"])
+    assert np.all(same["leak"] == 0.0)
+
+
+def test_truncated_trajectory_average_matches_truncated_density_matrix():
+    """The truncated sampler averages to the truncated AME (projected and
+    renormalised at each frame change) within 3.5 sigma at four grid points;
+    the per-trajectory renormalisation differs from the ensemble one only at
+    second order in the leakage, which is ~1e-4 here."""
+    inst = W.tfim_instance(3, 45, eta_g2=0.05, t_f=4.0, n_grid=41, seed=3, n_levels=4)
+    ref = ame.run(inst)
+    assert 1e-6 < ref["leak"].max() < 1e-2
+    M = 600
+    p, jumps, _, leak = trajectories.sample(inst, range(M), return_leak=True)
+    assert len(jumps) > 50
+    for k in (10, 20, 30, 40):
+        mean = p[:, k].mean()
+        se = max(p[:, k].std(ddof=1), 1e-3) / math.sqrt(M)
+        assert abs(mean - ref["p_gs"][k]) < 3.5 * se, (k, mean, ref["p_gs"][k], se)

@@ -52,6 +52,7 @@ class Instance:
     n_grid: int = 1000
     M: int = 1000             # trajectories
     seed: int = 1             # trajectory random-stream seed
+    n_levels: int = 0         # keep the lowest n_levels instantaneous eigenstates (0: all)
 
     @property
     def N(self) -> int:
