@@ -113,7 +113,8 @@ const char *aqt_last_error(const aqt_ctx *ctx);
 /* Ising terms of H_S (Sec. V, Eq. H_S, with the field sign written out):
  *   H(s) = A(s) (-sum_i sx_i) + B(s) (sum_i hz_i sz_i + sum_{i<j} Jzz_ij sz_i sz_j).
  * The paper's H^Z = -sum h sz + sum J sz sz maps to hz = -h.
- * n_qubits in [1, 10]; hz[n]; Jzz[n*n] row-major, entries with i < j used. */
+ * n_qubits in [1, 16] (above 10 only with aqt_set_levels); hz[n]; Jzz[n*n]
+ * row-major, entries with i < j used. */
 aqt_status aqt_set_ising(aqt_ctx *ctx, int n_qubits, const double *hz, const double *Jzz);
 
 /* Piecewise-linear annealing schedule through n_knots (s, A, B) points,
@@ -125,6 +126,25 @@ aqt_status aqt_set_schedule(aqt_ctx *ctx, int n_knots, const double *s, const do
  * independent sz coupling per qubit. lamb_shift = 1 adds
  * H_LS = sum S(w) L^dag L with S(w) = (1/2pi) P int gamma(x)/(w - x) dx (Sec. II; App. E). */
 aqt_status aqt_set_bath(aqt_ctx *ctx, double eta_g2, double omega_c, double beta, int lamb_shift);
+
+/* Truncated model: keep only the n_levels lowest instantaneous eigenstates of
+ * H_S(s) at every grid point (0, the default, or 2^n keeps all). The paper
+ * does not discuss truncation; its 16-qubit example (Sec. V.C) is where the
+ * full space is too large. Reading: the system's Hilbert space at s is the
+ * span of the kept eigenstates; the jump operators and the Lamb shift act
+ * within it (P A P); the frame change between grid points is the n_levels x
+ * n_levels block O = V_k^T V_{k-1}, which is not orthogonal: the weight it
+ * moves out of the kept levels (the leakage) is renormalised away with the
+ * rest of the rotation's norm change and never counted as jump probability
+ * (aqt_get_rotation_error reports the largest one of a run). The eigenpairs
+ * come from FP64 block Lanczos without forming H (2^n amplitudes per vector),
+ * warm-started along the grid; the cut must fall between degenerate
+ * manifolds at every grid point (at s = 0 of the transverse-field model the
+ * multiplicities are C(n, k), so allowed cuts are 1, 1 + n, 1 + n + C(n,2),
+ * ...), else aqt_build_tables returns AQT_EDEGEN. Device runs take
+ * n_levels <= 512; every source level's jump amplitudes are tabled, so the
+ * device needs no eigenvectors. */
+aqt_status aqt_set_levels(aqt_ctx *ctx, int n_levels);
 
 /* Shared time grid s_k = k/(n_grid-1), t_k = s_k t_f, n_grid >= 2. The generator
  * is frozen at s_{k-1} for the first half of [t_{k-1}, t_k] and at s_k for the
@@ -210,6 +230,13 @@ aqt_status aqt_get_observable_sums(aqt_ctx *ctx, double *sum_x, double *sum_x2);
 aqt_status aqt_observables_from_sums(int n_grid, int64_t M, const double *sum_x, const double *sum_x2,
                                      double *mean, double *stderr_);
 
+/* Per grid point g >= 1, the sum over trajectories of the frame rotation's
+ * norm loss 1 - |O c|^2 into s_g (c normalised): with aqt_set_levels, the
+ * leakage out of the kept levels at each step (divide by M for the mean);
+ * otherwise the rotation's rounding (O is orthogonal). sum_leak[n_grid],
+ * entry 0 is 0. */
+aqt_status aqt_get_leakage(aqt_ctx *ctx, double *sum_leak);
+
 /* Precision check of the frame rotation (its own arithmetic, as run): the
  * largest |(squared norm after a rotation c <- O c) / (before) - 1| over all
  * trajectories and grid steps of the last run. O is orthogonal, so this is
@@ -222,9 +249,10 @@ aqt_status aqt_get_rotation_error(aqt_ctx *ctx, double *max_rel);
 aqt_status aqt_get_jumps(aqt_ctx *ctx, aqt_jump *host_buf, int64_t cap, int64_t *n_out,
                          int64_t *n_dropped);
 
-/* Final normalised states at s = 1, host_buf[M][N][2] (re, im) FP64.
- * basis 0: instantaneous eigenbasis of H_S(1) (the library's eigenvector
- * signs); basis 1: computational basis. */
+/* Final normalised states at s = 1 (re, im) FP64. basis 0: instantaneous
+ * eigenbasis of H_S(1) (the library's eigenvector signs), host_buf[M][N][2]
+ * with N the levels carried; basis 1: computational basis,
+ * host_buf[M][2^n][2]. */
 aqt_status aqt_get_final_state(aqt_ctx *ctx, int basis, double *host_buf);
 
 /* Run without caller-provided scratch (the paper has no counterpart: this is
@@ -315,16 +343,19 @@ aqt_status aqt_batch_sync(aqt_batch *batch, int32_t *member_status);
  * (SIMT) or 128-level blocks (tensor cores); tiles). */
 aqt_status aqt_batch_get_shape(aqt_batch *batch, int member, int32_t *shape);
 
-/* Table inspection (tests). which: 0 eigenvalues [N]; 1 diag of H_eff,
+/* Table inspection (tests). N: the levels carried (aqt_set_levels), D = 2^n.
+ * which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes
  * R_alpha[a][b] = sqrt(gamma(E_b - E_a)) <a|sz_alpha|b>, [n][N][N] (FP64,
  * formed from the eigenvectors on request); 4 frame rotation
- * O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1); 5 eigenvectors V [N][N]
+ * O_g = V_{g+1}^T V_g [N][N] (g < n_grid-1); 5 eigenvectors V [D][N]
  * (column a = level a); 6 manifold energy per level [N]; 7 grid metadata [4]:
  * (some manifold degenerate, ground-manifold size, every Bohr class of
  * nonzero frequency is a single manifold pair, energy tolerance); 8 [2]:
  * (number of grid points that keep full jump amplitudes, bytes copied to the
- * device by the last aqt_build_tables; grid is ignored). */
+ * device by the last aqt_build_tables; grid is ignored); 9 [2]: (truncated
+ * model: the first eigenvalue above the kept levels at `grid`, the most
+ * block-Lanczos restarts any grid point needed). */
 aqt_status aqt_debug_table(aqt_ctx *ctx, int which, int grid, double *out);
 
 #ifdef __cplusplus

@@ -23,9 +23,9 @@ STATUS_NAMES = {0: "AQT_OK", 1: "AQT_EINVAL", 2: "AQT_ECUDA", 3: "AQT_ENOMEM", 4
                 10: "AQT_WDT"}
 
 EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_set_schedule",
-           "aqt_set_bath", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
+           "aqt_set_bath", "aqt_set_levels", "aqt_set_grid", "aqt_set_trajectories", "aqt_workspace_size",
            "aqt_bind_workspace", "aqt_build_tables", "aqt_get_dt_bounds", "aqt_set_wait_limit", "aqt_run", "aqt_sync", "aqt_get_observables",
-           "aqt_get_observable_sums", "aqt_observables_from_sums", "aqt_get_rotation_error", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
+           "aqt_get_observable_sums", "aqt_observables_from_sums", "aqt_get_rotation_error", "aqt_get_leakage", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
            "aqt_run_static_scratch", "aqt_batch_create", "aqt_batch_destroy", "aqt_batch_last_error",
            "aqt_batch_workspace_size", "aqt_batch_bind_workspace", "aqt_batch_tune", "aqt_batch_run", "aqt_batch_sync",
            "aqt_batch_get_shape"]
@@ -64,6 +64,7 @@ def lib():
             "aqt_set_ising": (I, [P, I, D, D]),
             "aqt_set_schedule": (I, [P, I, D, D, D]),
             "aqt_set_bath": (I, [P, C.c_double, C.c_double, C.c_double, I]),
+            "aqt_set_levels": (I, [P, I]),
             "aqt_set_grid": (I, [P, C.c_double, I]),
             "aqt_set_trajectories": (I, [P, I64, U64, I, I, I64]),
             "aqt_workspace_size": (I, [P, C.POINTER(SZ)]),
@@ -77,6 +78,7 @@ def lib():
             "aqt_get_observable_sums": (I, [P, D, D]),
             "aqt_observables_from_sums": (I, [I, I64, D, D, D, D]),
             "aqt_get_rotation_error": (I, [P, D]),
+            "aqt_get_leakage": (I, [P, D]),
             "aqt_get_jumps": (I, [P, C.POINTER(aqt_jump), I64, C.POINTER(I64), C.POINTER(I64)]),
             "aqt_get_final_state": (I, [P, I, D]),
             "aqt_debug_table": (I, [P, I, I, D]),
@@ -142,6 +144,10 @@ def aqt_set_schedule(ctx, s, A, B):
 
 def aqt_set_bath(ctx, eta_g2, omega_c, beta, lamb_shift):
     _check(ctx, lib().aqt_set_bath(ctx, float(eta_g2), float(omega_c), float(beta), int(bool(lamb_shift))))
+
+
+def aqt_set_levels(ctx, n_levels):
+    _check(ctx, lib().aqt_set_levels(ctx, int(n_levels)))
 
 
 def aqt_set_grid(ctx, t_f, n_grid):
@@ -216,6 +222,12 @@ def aqt_observables_from_sums(M: int, sum_x, sum_x2):
     return mean, se
 
 
+def aqt_get_leakage(ctx, n_grid: int):
+    out = np.empty(n_grid)
+    _check(ctx, lib().aqt_get_leakage(ctx, _dp(out)))
+    return out
+
+
 def aqt_get_rotation_error(ctx) -> float:
     v = C.c_double()
     _check(ctx, lib().aqt_get_rotation_error(ctx, C.byref(v)))
@@ -231,6 +243,7 @@ def aqt_get_jumps(ctx, cap: int):
 
 
 def aqt_get_final_state(ctx, basis: int, M: int, N: int):
+    """N: the levels carried (basis 0) or 2^n (basis 1)."""
     out = np.empty((M, N, 2))
     _check(ctx, lib().aqt_get_final_state(ctx, int(basis), _dp(out)))
     return out[..., 0] + 1j * out[..., 1]
@@ -317,7 +330,9 @@ class Session:
         self.inst = inst
         self.device = device
         self.M = int(inst.M if M is None else M)
-        self.N = 1 << inst.n_qubits
+        self.D = 1 << inst.n_qubits
+        nl = int(getattr(inst, "n_levels", 0) or 0)
+        self.N = nl if 0 < nl < self.D else self.D
         self.K = inst.n_grid
         self.ctx = aqt_create(device)
         self.jcap = int(jump_capacity if jump_capacity is not None else max(1024, 64 * self.M))
@@ -329,6 +344,7 @@ class Session:
         aqt_set_ising(c, inst.n_qubits, inst.hz, inst.J)
         aqt_set_schedule(c, inst.sched_s, inst.sched_A, inst.sched_B)
         aqt_set_bath(c, inst.eta_g2, inst.omega_c, inst.beta, inst.lamb_shift)
+        aqt_set_levels(c, int(getattr(inst, "n_levels", 0) or 0))
         aqt_set_grid(c, inst.t_f, inst.n_grid)
         aqt_set_trajectories(c, self.M, inst.seed if seed is None else seed, precision, timing, self.jcap)
 
@@ -359,7 +375,7 @@ class Session:
         return aqt_get_jumps(self.ctx, self.jcap)
 
     def final_state(self, basis=1):
-        return aqt_get_final_state(self.ctx, basis, self.M, self.N)
+        return aqt_get_final_state(self.ctx, basis, self.M, self.D if basis == 1 else self.N)
 
     def close(self):
         if self.ctx:

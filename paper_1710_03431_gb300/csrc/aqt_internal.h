@@ -32,6 +32,17 @@ struct Bath {
 
 bool sym_eigen(int n, double *A, double *evals, double *V);
 
+// The lowest eigenpairs of H = A (-sum_i sx_i) + B diag(Ez) on n qubits
+// (matrix-free Chebyshev-filtered subspace iteration, FP64, block of p
+// vectors), the lowest `want` converged to a residual of 1e-12 of the scale of
+// H. X0: p start vectors ([p][2^n], any norm) or null for fixed pseudo-random
+// ones. Out: evals[p] ascending (Ritz values), X [p][2^n] orthonormal,
+// *restarts: filter passes used, *next_lower: a lower estimate of the next
+// eigenvalue after the wanted ones (its Ritz value minus its residual). false
+// if not converged.
+bool lowest_eigen(int n, double A, double B, const double *Ez, int p, int want, const double *X0, double *evals,
+                  double *X, int *restarts, double *next_lower);
+
 // Allocator whose value-initialisation leaves trivial elements uninitialised:
 // the large tables are written in full by the (threaded) builder, so zero
 // filling them first only costs time.
@@ -69,9 +80,14 @@ struct GridMeta {
 
 struct Tables {
     int n = 0, N = 0, K = 0;
+    // basis dimension 2^n; N = D unless the lowest levels only are kept (N < D)
+    int D = 0;
+    bool truncated = false;
+    std::vector<double> ev_next;  // [K] truncated: the first eigenvalue above the kept levels
+    int lanczos_restarts = 0;     // truncated: largest number of restarts of one grid point
     double dt = 0.0, tau = 0.0;
     hvec<double> evals;          // [K][N]
-    hvec<double> V;              // [K][N][N]  row x, column a
+    hvec<double> V;              // [K][D][N]  row x, column a
     std::vector<double> kdiag;   // [K][N][2]  diag of the eigenframe H_eff
     std::vector<double> ehalf;   // [K][N][2]  exp(-i K_aa tau)
     std::vector<double> d2;      // [K][N]     exp(2 Im K_aa tau)
@@ -115,6 +131,9 @@ struct Inputs {
     int precision = 0;
     int timing = 0;
     int64_t jcap = 0;
+    int n_levels = 0;  // keep the lowest n_levels instantaneous levels (0: all)
+    // levels the trajectories carry: n_levels when it truncates, else 2^n
+    int levels() const { return (n_levels > 0 && n_levels < (1 << n)) ? n_levels : (1 << n); }
 };
 
 // Returns AQT_OK or an error with a message in *err.
@@ -159,8 +178,12 @@ struct RunParams {
     aqt_jump *jumps;
     int64_t jcap;
     unsigned long long *jcount;
-    double *obs_part;              // [n_cta][K][2]
+    // per-tile partials [n_cta][K][3]: sum of x, sum of x^2, sum of the frame
+    // rotation's norm loss 1 - |O c|^2 (the leakage of a truncated model; the
+    // rounding of the rotation otherwise)
+    double *obs_part;
     double *obs_sum;               // [K][2]
+    double *leak_sum;              // [K] sum of 1 - |O c|^2 over trajectories, or null
     double *scratch;               // [n_cta][kScratchSlots][kSlotDouble2 * N][2] jump scratch
     int32_t *status;
     // Poll limit of the tensor-core kernel's bounded waits between its roles

@@ -419,7 +419,8 @@ aqt_status aqt_batch_create(aqt_batch **out, aqt_ctx *const *members, int n_memb
     for (int f = 0; f < kForms; ++f) {
         if (b->members[f].empty()) continue;
         if (is_tc(f)) {
-            const int cap = tc_shape(f == kFormTc128 ? 128 : 256, (int64_t)1 << 40, 1);
+            // the largest tile the shared and tensor memory take (tc_shape from 256 per SM down)
+            const int cap = tc_shape(f == kFormTc128 ? 128 : 256, 256, 1);
             b->cands[f].push_back(cap);
             const int half = ((cap / 2) + 7) & ~7;
             if (half >= 16 && half < cap) b->cands[f].push_back(half);
@@ -468,7 +469,7 @@ aqt_status aqt_batch_create(aqt_batch **out, aqt_ctx *const *members, int n_memb
             size_t it = 0;
             for (int i : b->members[f]) {
                 it += tiles[i];
-                obs_need[i] = std::max(obs_need[i], (size_t)tiles[i] * b->mem[i].p.K * 16);
+                obs_need[i] = std::max(obs_need[i], (size_t)tiles[i] * b->mem[i].p.K * 24);
                 tt_max = std::max(tt_max, TT[i]);
             }
             items_f = std::max(items_f, it);

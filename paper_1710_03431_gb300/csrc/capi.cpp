@@ -17,7 +17,7 @@ using namespace aqt;
 
 struct Layout {
     size_t kdiag, ehalf, ehalf32, d2, G, Mdiag, V, Rlow, gslot, Rgen, lvlE, mfirst, msize, meta, OT, tclvl;
-    size_t final_state, jumps, jcount, obs_part, obs_sum, scratch, status, norm_err, total;
+    size_t final_state, jumps, jcount, obs_part, obs_sum, leak_sum, scratch, status, norm_err, total;
 };
 
 struct aqt_ctx {
@@ -81,7 +81,7 @@ void parallel_rows(size_t count, F f) {
 
 void compute_layout(aqt_ctx *c) {
     const Inputs &in = c->in;
-    const size_t n = in.n, N = (size_t)1 << in.n, K = in.K;
+    const size_t n = in.n, N = (size_t)in.levels(), K = in.K;
     const bool tc = in.precision == AQT_PREC_F16SPLIT;
     const size_t rs = in.precision == AQT_PREC_FP64 ? 8 : tc ? 4 : 4;
     if (tc) {
@@ -106,8 +106,10 @@ void compute_layout(aqt_ctx *c) {
     L.d2 = take(K * N * 8);
     L.G = take(K * n * N * 8);
     L.Mdiag = take(K * n * N * 8);
-    L.V = take(K * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
-    L.Rlow = take(K * n * std::min<size_t>(N, kLowSources) * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
+    // eigenvectors for the jump columns of sources above the tabled ones (none
+    // when truncated: every source is tabled)
+    L.V = take(c->tab.truncated ? 0 : K * N * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
+    L.Rlow = take(K * n * (size_t)c->tab.n_low * N * (in.precision == AQT_PREC_FP64 ? 8 : 4));
     L.gslot = take(K * 4);
     L.Rgen = take((size_t)c->tab.n_general * n * N * N * 8);
     L.lvlE = take(K * N * 8);
@@ -119,8 +121,9 @@ void compute_layout(aqt_ctx *c) {
     L.final_state = take((size_t)in.M * N * 2 * 8);
     L.jumps = take((size_t)std::max<int64_t>(in.jcap, 1) * sizeof(aqt_jump));
     L.jcount = take(8);
-    L.obs_part = take((size_t)c->n_cta * K * 2 * 8);
+    L.obs_part = take((size_t)c->n_cta * K * 3 * 8);
     L.obs_sum = take(K * 2 * 8);
+    L.leak_sum = take(K * 8);
     L.scratch = take(scratch_bytes(c->n_cta, (int)N, c->TT, tc));
     L.status = take(4);
     L.norm_err = take(4);
@@ -131,8 +134,9 @@ void compute_layout(aqt_ctx *c) {
 // warp holds N/32 levels per lane in registers, at most 16); the tensor-core
 // tiles take N = 128 or 256.
 aqt_status device_shape_check(aqt_ctx *c) {
-    if (c->in.n > 9) return fail(c, AQT_EINVAL, "device runs take n_qubits <= 9 (N <= 512)");
-    if (c->in.precision == AQT_PREC_F16SPLIT && (c->in.n < 7 || c->in.n > 8))
+    const int N = c->in.levels();
+    if (N > 512) return fail(c, AQT_EINVAL, "device runs take at most 512 levels (n_qubits <= 9, or aqt_set_levels)");
+    if (c->in.precision == AQT_PREC_F16SPLIT && N != 128 && N != 256)
         return fail(c, AQT_EINVAL, "the tensor-core path takes N = 128 or 256 (n_qubits 7 or 8)");
     if (c->in.precision == AQT_PREC_F16SPLIT && c->in.timing == AQT_JUMP_FIXED_STEP)
         return fail(c, AQT_EINVAL, "the fixed-step sampler runs on the SIMT paths (AQT_PREC_FP64, AQT_PREC_FP32)");
@@ -153,7 +157,7 @@ void fill_params(const aqt_ctx *c, RunParams *p) {
     const Inputs &in = c->in;
     *p = RunParams{};
     p->n = in.n;
-    p->N = 1 << in.n;
+    p->N = in.levels();
     p->K = in.K;
     p->TT = c->TT;
     p->RA = c->RA;
@@ -189,6 +193,7 @@ void fill_params(const aqt_ctx *c, RunParams *p) {
     p->jcount = (unsigned long long *)(c->ws + L.jcount);
     p->obs_part = (double *)(c->ws + L.obs_part);
     p->obs_sum = (double *)(c->ws + L.obs_sum);
+    p->leak_sum = (double *)(c->ws + L.leak_sum);
     p->scratch = (double *)(c->ws + L.scratch);
     p->status = (int32_t *)(c->ws + L.status);
     p->norm_err = (unsigned int *)(c->ws + L.norm_err);
@@ -243,8 +248,8 @@ aqt_status static_scratch_need(aqt_ctx *c, size_t *bytes) {
     if (s == AQT_OK) s = use_device(c);
     if (s != AQT_OK) return s;
     compute_layout(c);
-    const size_t N = (size_t)1 << c->in.n, K = c->in.K;
-    const size_t part = ((size_t)c->n_cta * K * 2 * 8 + 255) & ~(size_t)255;
+    const size_t N = (size_t)c->in.levels(), K = c->in.K;
+    const size_t part = ((size_t)c->n_cta * K * 3 * 8 + 255) & ~(size_t)255;
     *bytes = part + scratch_bytes(c->n_cta, (int)N, c->TT, c->in.precision == AQT_PREC_F16SPLIT);
     return AQT_OK;
 }
@@ -314,7 +319,7 @@ const char *aqt_last_error(const aqt_ctx *c) { return c ? c->err.c_str() : "null
 
 aqt_status aqt_set_ising(aqt_ctx *c, int n_qubits, const double *hz, const double *Jzz) {
     if (!c) return AQT_EINVAL;
-    if (n_qubits < 1 || n_qubits > 10) return fail(c, AQT_EINVAL, "n_qubits must be in [1, 10]");
+    if (n_qubits < 1 || n_qubits > 16) return fail(c, AQT_EINVAL, "n_qubits must be in [1, 16]");
     if (!hz || !Jzz) return fail(c, AQT_EINVAL, "hz and Jzz must be non-null");
     for (int i = 0; i < n_qubits; ++i)
         if (!std::isfinite(hz[i])) return fail(c, AQT_EINVAL, "hz has a non-finite entry");
@@ -355,6 +360,14 @@ aqt_status aqt_set_bath(aqt_ctx *c, double eta_g2, double omega_c, double beta, 
     c->in.bath.beta = beta;
     c->in.bath.lamb_shift = lamb_shift != 0;
     c->in.have_bath = true;
+    invalidate(c);
+    return AQT_OK;
+}
+
+aqt_status aqt_set_levels(aqt_ctx *c, int n_levels) {
+    if (!c) return AQT_EINVAL;
+    if (n_levels < 0 || n_levels > 65536) return fail(c, AQT_EINVAL, "n_levels must be in [0, 65536]");
+    c->in.n_levels = n_levels;
     invalidate(c);
     return AQT_OK;
 }
@@ -459,15 +472,17 @@ aqt_status aqt_build_tables(aqt_ctx *c, void *stream) {
     std::vector<float> lv;
     hvec<float> rl32;
     if (c->in.precision == AQT_PREC_FP64) {
-        if (!e) e = put(L.V, t.V.data(), t.V.size() * 8);
+        if (!e && !t.truncated) e = put(L.V, t.V.data(), t.V.size() * 8);
         if (!e) e = put(L.Rlow, t.Rlow.data(), t.Rlow.size() * 8);
         if (!e) e = put(L.OT, t.OT.data(), t.OT.size() * 8);
     } else {
-        v32.resize(K * NN);
-        parallel_rows(K, [&](size_t g) {
-            for (size_t i = 0; i < NN; ++i) v32[g * NN + i] = (float)t.V[g * NN + i];
-        });
-        if (!e) e = put(L.V, v32.data(), v32.size() * 4);
+        if (!t.truncated) {
+            v32.resize(K * NN);
+            parallel_rows(K, [&](size_t g) {
+                for (size_t i = 0; i < NN; ++i) v32[g * NN + i] = (float)t.V[g * NN + i];
+            });
+            if (!e) e = put(L.V, v32.data(), v32.size() * 4);
+        }
         rl32.assign(t.Rlow.begin(), t.Rlow.end());
         if (!e) e = put(L.Rlow, rl32.data(), rl32.size() * 4);
     }
@@ -582,6 +597,16 @@ aqt_status aqt_get_observable_sums(aqt_ctx *c, double *sum_x, double *sum_x2) {
     return AQT_OK;
 }
 
+aqt_status aqt_get_leakage(aqt_ctx *c, double *sum_leak) {
+    if (!c || !sum_leak) return AQT_EINVAL;
+    aqt_status s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (!c->ran) return fail(c, AQT_EINVAL, "run first");
+    cudaError_t e = cudaMemcpy(sum_leak, c->ws + c->lay.leak_sum, (size_t)c->in.K * 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, "leakage readback");
+    return AQT_OK;
+}
+
 aqt_status aqt_set_wait_limit(aqt_ctx *c, int64_t polls) {
     if (!c) return AQT_EINVAL;
     if (polls < 0 || polls > kDefaultWaitPolls) return fail(c, AQT_EINVAL, "poll limit must be in [0, 2^22]");
@@ -665,24 +690,28 @@ aqt_status aqt_get_final_state(aqt_ctx *c, int basis, double *host_buf) {
     aqt_status s = use_device(c);
     if (s != AQT_OK) return s;
     if (!c->ran) return fail(c, AQT_EINVAL, "run first");
-    const size_t N = (size_t)1 << c->in.n, M = (size_t)c->in.M;
-    cudaError_t e = cudaMemcpy(host_buf, c->ws + c->lay.final_state, M * N * 2 * 8, cudaMemcpyDeviceToHost);
+    const size_t N = (size_t)c->in.levels(), D = (size_t)1 << c->in.n, M = (size_t)c->in.M;
+    if (basis == 0) {
+        cudaError_t e = cudaMemcpy(host_buf, c->ws + c->lay.final_state, M * N * 2 * 8, cudaMemcpyDeviceToHost);
+        if (e) return cuda_fail(c, e, "final state readback");
+        return AQT_OK;
+    }
+    // computational basis: psi = V c with the eigenvectors of s = 1 (D x N)
+    std::vector<double> eig(M * N * 2);
+    cudaError_t e = cudaMemcpy(eig.data(), c->ws + c->lay.final_state, M * N * 2 * 8, cudaMemcpyDeviceToHost);
     if (e) return cuda_fail(c, e, "final state readback");
-    if (basis == 1) {
-        const double *V = &c->tab.V[(size_t)(c->in.K - 1) * N * N];
-        std::vector<double> tmp(N * 2);
-        for (size_t m = 0; m < M; ++m) {
-            double *cm = host_buf + m * N * 2;
-            for (size_t x = 0; x < N; ++x) {
-                double re = 0.0, im = 0.0;
-                for (size_t a = 0; a < N; ++a) {
-                    re += V[x * N + a] * cm[2 * a];
-                    im += V[x * N + a] * cm[2 * a + 1];
-                }
-                tmp[2 * x] = re;
-                tmp[2 * x + 1] = im;
+    const double *V = &c->tab.V[(size_t)(c->in.K - 1) * D * N];
+    for (size_t m = 0; m < M; ++m) {
+        const double *cm = &eig[m * N * 2];
+        double *out = host_buf + m * D * 2;
+        for (size_t x = 0; x < D; ++x) {
+            double re = 0.0, im = 0.0;
+            for (size_t a = 0; a < N; ++a) {
+                re += V[x * N + a] * cm[2 * a];
+                im += V[x * N + a] * cm[2 * a + 1];
             }
-            std::memcpy(cm, tmp.data(), N * 2 * 8);
+            out[2 * x] = re;
+            out[2 * x + 1] = im;
         }
     }
     return AQT_OK;
@@ -704,7 +733,7 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
             for (size_t a = 0; a < N; ++a)
                 for (size_t b = 0; b < N; ++b) out[a * N + b] = t.OT[g * NN + b * N + a];
             break;
-        case 5: std::copy_n(&t.V[g * NN], NN, out); break;
+        case 5: std::copy_n(&t.V[g * (size_t)t.D * N], (size_t)t.D * N, out); break;
         case 6: std::copy_n(&t.lvlE[g * N], N, out); break;
         case 7:
             out[0] = t.meta[g].degenerate;
@@ -715,6 +744,10 @@ aqt_status aqt_debug_table(aqt_ctx *c, int which, int grid, double *out) {
         case 8:
             out[0] = t.n_general;
             out[1] = (double)c->uploaded;
+            break;
+        case 9:  // truncated: the first eigenvalue above the kept levels, and the most Lanczos restarts of a point
+            out[0] = t.truncated ? t.ev_next[g] : 0.0;
+            out[1] = t.lanczos_restarts;
             break;
         default: return fail(c, AQT_EINVAL, "unknown table");
     }

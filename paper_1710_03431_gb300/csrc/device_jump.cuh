@@ -45,7 +45,7 @@ namespace aqt {
 namespace dev {
 
 constexpr int kMaxJumpsPerHalf = 64;
-constexpr int kMaxAlpha = 10;
+constexpr int kMaxAlpha = 16;
 enum : int32_t { kStatusNumeric = 2, kStatusTimeout = 4 };
 
 template <typename T>

@@ -17,32 +17,32 @@ constexpr int kThreads = 256;  // threads of a SIMT CTA (simt_kernel.cuh)
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunkBytes = 32768;
 
-// Sum of the per-tile observable partials of one instance, in tile order
-// (fixed order: the same bits for any launch shape of the same tiles).
-__global__ void reduce_obs(const double *part, double *sum, int n_cta, int K) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= K) return;
-    double s = 0.0, s2 = 0.0;
-    for (int c = 0; c < n_cta; ++c) {
-        s += part[((size_t)c * K + g) * 2];
-        s2 += part[((size_t)c * K + g) * 2 + 1];
+// Sum of the per-tile observable partials ([tile][g][3]) of one instance, in
+// tile order (fixed order: the same bits for any launch shape of the same
+// tiles).
+__device__ __forceinline__ void reduce_one(const RunParams &p, int g) {
+    double s = 0.0, s2 = 0.0, sl = 0.0;
+    for (int c = 0; c < p.n_cta; ++c) {
+        const double *q = p.obs_part + ((size_t)c * p.K + g) * 3;
+        s += q[0];
+        s2 += q[1];
+        sl += q[2];
     }
-    sum[2 * g] = s;
-    sum[2 * g + 1] = s2;
+    p.obs_sum[2 * g] = s;
+    p.obs_sum[2 * g + 1] = s2;
+    if (p.leak_sum) p.leak_sum[g] = sl;
+}
+
+__global__ void reduce_obs(const __grid_constant__ RunParams p) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < p.K) reduce_one(p, g);
 }
 
 // The same for every instance of a batch: block y = instance.
 __global__ void reduce_obs_batch(const RunParams *ps) {
     const RunParams &p = ps[blockIdx.y];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.K) return;
-    double s = 0.0, s2 = 0.0;
-    for (int c = 0; c < p.n_cta; ++c) {
-        s += p.obs_part[((size_t)c * p.K + g) * 2];
-        s2 += p.obs_part[((size_t)c * p.K + g) * 2 + 1];
-    }
-    p.obs_sum[2 * g] = s;
-    p.obs_sum[2 * g + 1] = s2;
+    if (g < p.K) reduce_one(p, g);
 }
 
 }  // namespace
@@ -52,7 +52,7 @@ size_t simt_smem_bytes(int N, int TT, int precision) {
     const int LD = TT + 4;
     const int KB = std::min(N, std::max(1, kChunkBytes / (int)(N * rs)));
     size_t b = 0;
-    b += 2 * (size_t)N * 8 + 2 * (size_t)TT * 8 + 2 * kWarps * 8;  // d2s, gam, logr, ell, obs
+    b += 2 * (size_t)N * 8 + 3 * (size_t)TT * 8 + 3 * kWarps * 8;  // d2s, gam, logr, ell, leak, obs
     b += (size_t)((TT + 3) & ~3) * 4;                           // nj
     b += 2 * (size_t)N * LD * rs;                               // cre, cim
     b += (size_t)KB * N * rs;                                   // O chunk
@@ -92,7 +92,7 @@ int launch_run(const RunParams &p, int precision, void *stream, size_t smem) {
             : precision == AQT_PREC_FP64   ? launch_simt_f64(p, stream, smem)
                                            : launch_simt_f32(p, stream, smem);
     if (e) return e;
-    reduce_obs<<<(p.K + 127) / 128, 128, 0, st>>>(p.obs_part, p.obs_sum, p.n_cta, p.K);
+    reduce_obs<<<(p.K + 127) / 128, 128, 0, st>>>(p);
     return (int)cudaGetLastError();
 }
 

@@ -653,8 +653,9 @@ __device__ __forceinline__ bool tc_tile(const RunParams &p, int cta, unsigned ch
             }
             warp_sum2(sx, sx2);
             if (lane == 0) {
-                p.obs_part[((size_t)cta * K) * 2] = sx;
-                p.obs_part[((size_t)cta * K) * 2 + 1] = sx2;
+                p.obs_part[((size_t)cta * K) * 3] = sx;
+                p.obs_part[((size_t)cta * K) * 3 + 1] = sx2;
+                p.obs_part[((size_t)cta * K) * 3 + 2] = 0.0;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1058,18 +1059,22 @@ __device__ __forceinline__ bool tc_tile(const RunParams &p, int cta, unsigned ch
             }
             // ---- observable partials (fixed order) -----------------------------------------
             if (e == 0) {
-                // per-CTA partials in FP64 (the per-trajectory values are FP32)
-                double sx = 0.0, sx2 = 0.0;
+                // per-CTA partials in FP64 (the per-trajectory values are FP32),
+                // with the rotation's norm loss 1 - P
+                double sx = 0.0, sx2 = 0.0, sl = 0.0;
                 for (int t = lane; t < TT; t += 32) {
                     if (S.flag[t] == 2) continue;
                     const double x = S.x[t];
                     sx += x;
                     sx2 += x * x;
+                    sl += 1.0 - (double)S.P[t];
                 }
                 warp_sum2(sx, sx2);
+                sl = warp_sum(sl);
                 if (lane == 0) {
-                    p.obs_part[((size_t)cta * K + g) * 2] = sx;
-                    p.obs_part[((size_t)cta * K + g) * 2 + 1] = sx2;
+                    p.obs_part[((size_t)cta * K + g) * 3] = sx;
+                    p.obs_part[((size_t)cta * K + g) * 3 + 1] = sx2;
+                    p.obs_part[((size_t)cta * K + g) * 3 + 2] = sl;
                 }
             }
         }

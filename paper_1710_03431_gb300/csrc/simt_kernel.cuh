@@ -79,7 +79,7 @@ __device__ __forceinline__ const double *ehalf_table<double>(const RunParams &p)
 template <typename R>
 __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t traj, R *cre, R *cim, int LD,
                           const R *eh, const double *d2s, const double *gam, Scalars sc, double2 *c64, int lane,
-                          float *nerr) {
+                          float *nerr, double *leak) {
     const int N = p.N;
     double nu = 0.0, f = 0.0;
     for (int a = lane; a < N; a += 32) {
@@ -94,7 +94,10 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
         if (lane == 0) atomicOr(p.status, kStatusNumeric);
         return;
     }
-    if (half == 0 && g > 0) *nerr = fmaxf(*nerr, (float)fabs(nu - 1.0));
+    if (half == 0 && g > 0) {
+        *nerr = fmaxf(*nerr, (float)fabs(nu - 1.0));
+        if (lane == 0) leak[t] = 1.0 - nu;  // the rotation's norm loss (leakage when truncated)
+    }
     if (p.timing == kTimingFixed) {
         // App. B.1: jump with probability tau lambda, lambda = sum_b |c_b|^2 Gamma_b / nu
         double lam = 0.0;
@@ -141,7 +144,7 @@ __device__ void half_step(const RunParams &p, int g, int half, int t, int64_t tr
 // The whole run of tile `cta` of one instance (trajectories cta*TT ..
 // cta*TT + TT - 1): states in shared memory (smem, simt_smem_bytes(N, TT)),
 // jump scratch at scr (kScratchSlots x kSlotDouble2 x N double2, one slot per
-// warp), observable partials at p.obs_part[cta][g]. RA: rows of the rotation
+// warp), observable partials at p.obs_part[cta][g][3]. RA: rows of the rotation
 // per thread; RA x (kThreads / (TT/4)) >= N.
 template <typename R, int RA>
 __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *scr, unsigned char *smem) {
@@ -155,8 +158,9 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
     double *gam = d2s + N;  // -2 Im K_aa: the level's total jump rate
     double *logr = gam + N;
     double *ell = logr + TT;
-    double *obs = ell + TT;                         // [kWarps][2]
-    int *nj = reinterpret_cast<int *>(obs + 2 * kWarps);
+    double *obs = ell + TT;                         // [kWarps][3]
+    double *leak = obs + 3 * kWarps;                // [TT] this step's norm loss of the rotation
+    int *nj = reinterpret_cast<int *>(leak + TT);
     R *cre = reinterpret_cast<R *>(nj + ((TT + 3) & ~3));
     R *cim = cre + (size_t)N * LD;
     R *osm = cim + (size_t)N * LD;
@@ -175,6 +179,7 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
     }
     for (int t = tid; t < TT; t += kThreads) {
         ell[t] = 0.0;
+        leak[t] = 0.0;
         nj[t] = 0;
         logr[t] = (t0 + t < p.M) ? log(uniform01(traj_event(p.seed, t0 + t, 0).x[0])) : 0.0;
     }
@@ -189,7 +194,7 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
     };
     const int gs0 = p.tab.meta[0].gs_size;
     auto observe = [&](int g, int gs) {
-        double wx = 0.0, wx2 = 0.0;
+        double wx = 0.0, wx2 = 0.0, wl = 0.0;
         for (int t = warp; t < TT; t += kWarps) {
             if (t0 + t >= p.M) continue;
             double x = 0.0;
@@ -200,27 +205,32 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
             x = warp_sum(x);
             wx += x;
             wx2 += x * x;
+            wl += leak[t];
         }
         if (lane == 0) {
-            obs[2 * warp] = wx;
-            obs[2 * warp + 1] = wx2;
+            obs[3 * warp] = wx;
+            obs[3 * warp + 1] = wx2;
+            obs[3 * warp + 2] = wl;
         }
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0, s2 = 0.0;
+            double s = 0.0, s2 = 0.0, sl = 0.0;
             for (int w = 0; w < kWarps; ++w) {
-                s += obs[2 * w];
-                s2 += obs[2 * w + 1];
+                s += obs[3 * w];
+                s2 += obs[3 * w + 1];
+                sl += obs[3 * w + 2];
             }
-            p.obs_part[((size_t)cta * K + g) * 2] = s;
-            p.obs_part[((size_t)cta * K + g) * 2 + 1] = s2;
+            double *q = p.obs_part + ((size_t)cta * K + g) * 3;
+            q[0] = s;
+            q[1] = s2;
+            q[2] = sl;
         }
     };
     float nerr = 0.0f;
     auto half_all = [&](int g, int half) {
         for (int t = warp; t < TT; t += kWarps) {
             if (t0 + t >= p.M) continue;
-            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, gam, sc, c64, lane, &nerr);
+            half_step<R>(p, g, half, t, t0 + t, cre, cim, LD, eh, d2s, gam, sc, c64, lane, &nerr, leak);
         }
     };
 

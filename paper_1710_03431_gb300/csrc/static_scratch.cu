@@ -113,11 +113,12 @@ extern "C" aqt_status aqt_run_static_scratch(aqt_ctx *ctx, void *stream, double 
     // vectors. Every element the kernel reads is written earlier in the same
     // call, so nothing here has to start at zero.
     unsigned char *b = static_cast<unsigned char *>(base);
-    const size_t part_bytes = (size_t)p.n_cta * p.K * 2 * sizeof(double);
+    const size_t part_bytes = (size_t)p.n_cta * p.K * 3 * sizeof(double);
     p.obs_part = reinterpret_cast<double *>(b);
     p.scratch = reinterpret_cast<double *>(b + ((part_bytes + 255) & ~(size_t)255));
     // Outputs belong to the caller; the two counters must start at zero.
     p.obs_sum = obs_sums;
+    p.leak_sum = nullptr;  // the leakage sums are not recorded here
     p.final_state = final_states;
     p.jumps = jumps;
     p.jcap = jump_capacity;

@@ -163,6 +163,37 @@ void sz_frames(const double *V, int n, double *M) {
         }
 }
 
+// The same for a truncated eigenvector table: V row-major [x][a] with D = 2^n
+// rows and L columns, M[alpha][a][b] for a, b < L. W_alpha = sum over rows
+// with bit alpha set of V[x][a] V[x][b], formed as a Gram matrix of those rows.
+void sz_frames_rect(const double *V, int n, int L, double *M) {
+    const size_t D = (size_t)1 << n, LL = (size_t)L * L;
+    std::vector<double> Xa((size_t)L * (D / 2)), W(LL);
+    for (int al = 0; al < n; ++al) {
+        // columns of V over the rows with bit alpha set, vector-major
+        size_t k = 0;
+        for (size_t x = 0; x < D; ++x) {
+            if (!((x >> al) & 1)) continue;
+            for (int a = 0; a < L; ++a) Xa[(size_t)a * (D / 2) + k] = V[x * L + a];
+            ++k;
+        }
+        gram(Xa.data(), Xa.data(), L, L, (int)(D / 2), W.data(), L, true);
+        double *Ma = M + (size_t)al * LL;
+        for (int a = 0; a < L; ++a)
+            for (int b = a; b < L; ++b) {
+                const double v = (a == b ? 1.0 : 0.0) - 2.0 * W[(size_t)a * L + b];
+                Ma[(size_t)a * L + b] = v;
+                Ma[(size_t)b * L + a] = v;
+            }
+    }
+}
+
+// M_alpha for every qubit from the eigenvector table of one grid point.
+void frames_of(const Tables &tab, const double *V, double *M) {
+    if (tab.truncated) sz_frames_rect(V, tab.n, tab.N, M);
+    else sz_frames(V, tab.n, M);
+}
+
 // Ascending sort of non-negative doubles (their bit patterns order like the
 // values): least-significant-digit radix sort, 11-bit digits.
 void sort_nonnegative(std::vector<double> &w) {
@@ -191,21 +222,32 @@ void schedule_at(const Inputs &in, double s, double *A, double *B) {
 }  // namespace
 
 aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
-    const int n = in.n, N = 1 << n, K = in.K;
+    const int n = in.n, D = 1 << n, N = in.levels(), K = in.K;
+    const bool trunc = N < D;
+    if (!trunc && n > 10) {
+        *err = "more than 10 qubits need a truncation to the lowest levels (aqt_set_levels)";
+        return AQT_EINVAL;
+    }
     tab.n = n;
     tab.N = N;
+    tab.D = D;
+    tab.truncated = trunc;
     tab.K = K;
     tab.dt = in.t_f / (K - 1);
     tab.tau = 0.5 * tab.dt;
-    const size_t NN = (size_t)N * N;
+    const size_t NN = (size_t)N * N, DN = (size_t)D * N;
     tab.evals.resize((size_t)K * N);  // written in full below
-    tab.V.resize((size_t)K * NN);
+    tab.V.resize((size_t)K * DN);
+    tab.ev_next.assign(trunc ? K : 0, 0.0);
+    tab.lanczos_restarts = 0;
     tab.kdiag.assign((size_t)K * N * 2, 0.0);
     tab.ehalf.assign((size_t)K * N * 2, 0.0);
     tab.d2.assign((size_t)K * N, 0.0);
     tab.G.assign((size_t)K * n * N, 0.0);
     tab.Mdiag.assign((size_t)K * n * N, 0.0);
-    tab.n_low = std::min(N, kLowSources);
+    // truncated: every source level's jump amplitudes are tabled (the device
+    // then needs no eigenvectors: they have 2^n rows)
+    tab.n_low = trunc ? N : std::min(N, kLowSources);
     tab.Rlow.resize((size_t)K * n * tab.n_low * N);
     tab.gslot.assign(K, -1);
     tab.n_general = 0;
@@ -217,13 +259,11 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     tab.OT.resize((size_t)(K - 1) * NN);
 
     // classical energies sum_i hz_i z_i + sum_{i<j} J_ij z_i z_j, z = 1 - 2 bit
-    std::vector<double> Ez(N, 0.0);
-    std::vector<int8_t> z((size_t)n * N);
-    for (int x = 0; x < N; ++x) {
+    std::vector<double> Ez(D, 0.0);
+    for (int x = 0; x < D; ++x) {
         double e = 0.0;
         for (int i = 0; i < n; ++i) {
             const int zi = 1 - 2 * ((x >> i) & 1);
-            z[(size_t)i * N + x] = (int8_t)zi;
             e += in.hz[i] * zi;
         }
         for (int i = 0; i < n; ++i)
@@ -243,18 +283,53 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     };
 
     // ---- pass 1: eigensystems ----------------------------------------------
-    parallel_for(K, [&](int g) {
-        const double s = (double)g / (K - 1);
-        double A, B;
-        schedule_at(in, s, &A, &B);
-        std::vector<double> H(NN, 0.0);
-        for (int x = 0; x < N; ++x) {
-            H[(size_t)x * N + x] = B * Ez[x];
-            for (int i = 0; i < n; ++i) H[(size_t)x * N + (x ^ (1 << i))] = -A;
-        }
-        if (!sym_eigen(N, H.data(), &tab.evals[(size_t)g * N], &tab.V[(size_t)g * NN]))
-            fail(AQT_ENOCONV, "eigensolver did not converge at grid point " + std::to_string(g));
-    });
+    if (!trunc) {
+        parallel_for(K, [&](int g) {
+            const double s = (double)g / (K - 1);
+            double A, B;
+            schedule_at(in, s, &A, &B);
+            std::vector<double> H(NN, 0.0);
+            for (int x = 0; x < N; ++x) {
+                H[(size_t)x * N + x] = B * Ez[x];
+                for (int i = 0; i < n; ++i) H[(size_t)x * N + (x ^ (1 << i))] = -A;
+            }
+            if (!sym_eigen(N, H.data(), &tab.evals[(size_t)g * N], &tab.V[(size_t)g * NN]))
+                fail(AQT_ENOCONV, "eigensolver did not converge at grid point " + std::to_string(g));
+        });
+    } else {
+        // the lowest N eigenpairs (the block carries guard vectors; the next
+        // eigenvalue is bounded from below to check the cut) by the
+        // Chebyshev-filtered block solver; the grid splits into one contiguous
+        // chunk per thread, each point warm-started from the previous one's vectors
+        const int p = std::min(D, N + std::max(8, N / 4)), want = N;
+        const int nchunk = std::max(1, std::min<int>(K, (int)n_threads()));
+        std::atomic<int> worst_restarts{0};
+        parallel_for(nchunk, [&](int c) {
+            const int g0 = (int)((int64_t)K * c / nchunk), g1 = (int)((int64_t)K * (c + 1) / nchunk);
+            std::vector<double> X((size_t)p * D), Xprev((size_t)p * D), ev(p);
+            for (int g = g0; g < g1; ++g) {
+                double A, B;
+                schedule_at(in, (double)g / (K - 1), &A, &B);
+                int it = 0;
+                double lower = INFINITY;
+                if (!lowest_eigen(n, A, B, Ez.data(), p, want, g == g0 ? nullptr : Xprev.data(), ev.data(), X.data(),
+                                  &it, &lower)) {
+                    fail(AQT_ENOCONV, "the block eigensolver did not converge at grid point " + std::to_string(g));
+                    return;
+                }
+                int w = worst_restarts.load();
+                while (it > w && !worst_restarts.compare_exchange_weak(w, it)) {
+                }
+                std::copy_n(ev.data(), N, &tab.evals[(size_t)g * N]);
+                tab.ev_next[g] = lower;
+                double *Vg = &tab.V[(size_t)g * DN];
+                for (int x = 0; x < D; ++x)
+                    for (int a = 0; a < N; ++a) Vg[(size_t)x * N + a] = X[(size_t)a * D + x];
+                Xprev.swap(X);
+            }
+        });
+        tab.lanczos_restarts = worst_restarts.load();
+    }
     if (st != AQT_OK) return st;
 
     double wmax = 10.0;
@@ -266,10 +341,15 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     // ---- pass 2: manifolds, M_alpha, rates, H_eff ----------------------------
     parallel_for(K, [&](int g) {
         const double *ev = &tab.evals[(size_t)g * N];
-        const double *V = &tab.V[(size_t)g * NN];
+        const double *V = &tab.V[(size_t)g * DN];
         double emax = 1.0;
         for (int a = 0; a < N; ++a) emax = std::max(emax, std::fabs(ev[a]));
         const double tol = 1e-12 * emax;
+        if (trunc && !(tab.ev_next[g] - ev[N - 1] > tol)) {
+            fail(AQT_EDEGEN, "keeping " + std::to_string(N) + " levels splits a degenerate manifold (or the next " +
+                                 "level could not be separated from the kept ones) at grid point " + std::to_string(g));
+            return;
+        }
         GridMeta &meta = tab.meta[g];
         meta.tol = tol;
         double *lvlE = &tab.lvlE[(size_t)g * N];
@@ -325,7 +405,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
         }
         std::vector<double> Mbuf((size_t)n * NN);
         double *Mg = Mbuf.data();
-        sz_frames(V, n, Mg);
+        frames_of(tab, V, Mg);
         // rates: gamma and S per level pair (a <- b), reused over alpha
         std::vector<double> gam(NN), lam(NN);
         for (int a = 0; a < N; ++a)
@@ -431,7 +511,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     // with a jump probability above 1e-6 over the whole run.
     {
         double hz_max = 0.0;
-        for (int x = 0; x < N; ++x) hz_max = std::max(hz_max, std::fabs(Ez[x]));
+        for (int x = 0; x < D; ++x) hz_max = std::max(hz_max, std::fabs(Ez[x]));
         for (int i = 0; i < 3; ++i) {
             tab.dt_bound[i] = INFINITY;
             tab.dt_bound_at[i] = 0;
@@ -472,16 +552,18 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     }
 
     // ---- pass 3: frame rotations OT_g[b][a] = (V_g^T V_{g+1})[b][a] ------------
+    // (truncated: N x N blocks of the rotation between the kept spans, not
+    // orthogonal; the weight they lose is the leakage the kernels renormalise away)
     parallel_for(K - 1, [&](int g) {
-        const double *V0 = &tab.V[(size_t)g * NN];
-        const double *V1 = &tab.V[(size_t)(g + 1) * NN];
-        std::vector<double> T0(NN), T1(NN);
-        for (int x = 0; x < N; ++x)
+        const double *V0 = &tab.V[(size_t)g * DN];
+        const double *V1 = &tab.V[(size_t)(g + 1) * DN];
+        std::vector<double> T0(DN), T1(DN);
+        for (int x = 0; x < D; ++x)
             for (int a = 0; a < N; ++a) {
-                T0[(size_t)a * N + x] = V0[(size_t)x * N + a];
-                T1[(size_t)a * N + x] = V1[(size_t)x * N + a];
+                T0[(size_t)a * D + x] = V0[(size_t)x * N + a];
+                T1[(size_t)a * D + x] = V1[(size_t)x * N + a];
             }
-        gram(T0.data(), T1.data(), N, N, N, &tab.OT[(size_t)g * NN], N, false);
+        gram(T0.data(), T1.data(), N, N, D, &tab.OT[(size_t)g * NN], N, false);
     });
     return AQT_OK;
 }
@@ -489,7 +571,7 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
 void jump_amplitudes(const Inputs &in, const Tables &tab, int g, double *out) {
     const int n = tab.n, N = tab.N;
     const size_t NN = (size_t)N * N;
-    sz_frames(&tab.V[(size_t)g * NN], n, out);  // M_alpha[a][b]
+    frames_of(tab, &tab.V[(size_t)g * tab.D * N], out);  // M_alpha[a][b]
     const double *lvlE = &tab.lvlE[(size_t)g * N];
     for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) {

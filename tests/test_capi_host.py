@@ -41,7 +41,9 @@ def test_argument_validation(aqt_lib):
         A.aqt_set_ising(c, 0, [1.0], [0.0])
     assert e.value.status == A.AQT_EINVAL
     with pytest.raises(A.AqtError):
-        A.aqt_set_ising(c, 11, np.zeros(11), np.zeros(121))
+        A.aqt_set_ising(c, 17, np.zeros(17), np.zeros(289))
+    with pytest.raises(A.AqtError):
+        A.aqt_set_levels(c, -1)
     with pytest.raises(A.AqtError):
         A.aqt_set_schedule(c, [0.0, 0.5], [1, 1], [0, 1])          # does not reach 1
     with pytest.raises(A.AqtError):
@@ -105,6 +107,69 @@ def test_tables_match_oracle(aqt_lib, n, seed, s_idx):
             O = A.aqt_debug_table(c, 4, g, (N, N))
             V1 = A.aqt_debug_table(c, 5, g + 1, (N, N))
             assert np.max(np.abs(O - V1.T @ V)) < 1e-13
+    A.aqt_destroy(c)
+
+
+@pytest.mark.parametrize("n,levels,seed,s_idx", [(6, 22, 17, [0, 1, 6, 10]), (8, 37, 23, [0, 3, 10])])
+def test_truncated_tables_match_oracle(aqt_lib, n, levels, seed, s_idx):
+    """Tables of the truncated model (lowest levels only, eigenpairs from the
+    library's matrix-free FP64 block solver) against the oracle's dense
+    eigensystem restricted to the same levels."""
+    A = aqt_lib
+    inst = W.tfim_instance(n, seed, n_grid=11, n_levels=levels)
+    N, D = levels, 1 << n
+    c = _host_ctx(A, inst)
+    A.aqt_set_levels(c, levels)
+    A.aqt_build_tables(c, 0)
+    for g in s_idx:
+        fr = lindblad.Frame(inst, g / 10)
+        ev = A.aqt_debug_table(c, 0, g, (N,))
+        np.testing.assert_allclose(ev, fr.eig.evals, atol=1e-10)
+        kd = A.aqt_debug_table(c, 1, g, (N, 2))
+        Kd = kd[:, 0] + 1j * kd[:, 1]
+        np.testing.assert_allclose(Kd.imag, np.diag(fr.K).imag, atol=1e-12)
+        np.testing.assert_allclose(Kd.real, np.diag(fr.K).real, atol=1e-8)   # Lamb-shift tables
+        V = A.aqt_debug_table(c, 5, g, (D, N))
+        assert np.max(np.abs(V.T @ V - np.eye(N))) < 1e-12
+        # the kept span and its spectral projector agree, whatever the basis inside
+        # degenerate manifolds
+        P, Po = V @ np.diag(ev) @ V.T, fr.eig.V @ np.diag(fr.eig.evals) @ fr.eig.V.T
+        assert np.max(np.abs(P - Po)) < 1e-10
+        nxt = A.aqt_debug_table(c, 9, g, (2,))[0]
+        assert nxt > ev[-1] + 1e-6
+        if fr.eig.nondegenerate:
+            G = A.aqt_debug_table(c, 2, g, (n, N))
+            Go = np.sum(fr.gam[None] * fr.M ** 2, axis=1)
+            np.testing.assert_allclose(G, Go, rtol=1e-9, atol=1e-14)
+        if g < 10:
+            O = A.aqt_debug_table(c, 4, g, (N, N))
+            V1 = A.aqt_debug_table(c, 5, g + 1, (D, N))
+            assert np.max(np.abs(O - V1.T @ V)) < 1e-12
+            sv = np.linalg.svd(O, compute_uv=False)
+            assert sv.max() <= 1 + 1e-12 and sv.min() < 1  # a contraction that leaks
+    A.aqt_destroy(c)
+
+
+def test_truncation_splitting_a_manifold_rejected(aqt_lib):
+    """At s = 0 the 6-qubit levels have multiplicities 1, 6, 15, ...: keeping
+    20 levels would cut the 15-fold manifold."""
+    A = aqt_lib
+    inst = W.tfim_instance(6, 17, n_grid=5)
+    c = _host_ctx(A, inst)
+    A.aqt_set_levels(c, 20)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_build_tables(c, 0)
+    assert e.value.status == A.AQT_EDEGEN and "splits" in str(e.value)
+    A.aqt_destroy(c)
+
+
+def test_eleven_qubits_need_truncation(aqt_lib):
+    A = aqt_lib
+    inst = W.tfim_instance(11, 5, n_grid=3)
+    c = _host_ctx(A, inst)
+    with pytest.raises(A.AqtError) as e:
+        A.aqt_build_tables(c, 0)
+    assert e.value.status == A.AQT_EINVAL and "aqt_set_levels" in str(e.value)
     A.aqt_destroy(c)
 
 
