@@ -23,6 +23,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -41,9 +43,10 @@ def parse():
                     help="timed steps (default: 60 for f16split, 3 for fp32 / fp64, 5 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="main", choices=["main", "small", "batch"],
+    ap.add_argument("--config", default="main", choices=["main", "small", "batch", "grad"],
                     help="main: 8 qubits, N = 256 (default); small: 4 qubits, N = 16; batch: 64 instances of "
-                         "6-8 qubits in one batched launch")
+                         "6-8 qubits in one batched launch; grad: d<P_GS(1)>/dtheta of the 8-qubit instance with an "
+                         "8-knot schedule, M = 2^14 (adjoint sweep against the forward run)")
     ap.add_argument("--batch-qubits", default="6,7,8", help="batch: qubit counts cycled over the instances")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--precision", default=None, choices=["f16split", "fp32", "fp64"],
@@ -58,9 +61,9 @@ def parse():
     ap.add_argument("--cpu-sample-traj", type=int, default=2000)
     a = ap.parse_args()
     if a.precision is None:
-        a.precision = "fp64" if a.config == "small" else "f16split"
+        a.precision = {"small": "fp64", "grad": "fp32"}.get(a.config, "f16split")
     if a.M is None:
-        a.M = {"main": 10_000, "small": 1000, "batch": 2048}[a.config]
+        a.M = {"main": 10_000, "small": 1000, "batch": 2048, "grad": 1 << 14}[a.config]
     if a.n_grid is None:
         a.n_grid = 2000 if a.config == "main" else 1000
     if a.tf is None:
@@ -72,6 +75,8 @@ def workload(args):
     import workloads as W
     if args.config == "small":
         return W.cfg_small(t_f=args.tf, M=args.M, n_grid=args.n_grid)
+    if args.config == "grad":
+        return W.cfg_grad(t_f=args.tf, M=args.M, n_grid=args.n_grid)
     return W.cfg_main(t_f=args.tf, M=args.M, n_grid=args.n_grid)
 
 
@@ -569,12 +574,101 @@ def run_batch(args):
         S.close()
 
 
+# ------------------------------------------------------------------- grad -----
+def run_grad(args):
+    """Gradient of <P_GS(1)> in the 2 x 8 schedule control values, 8 fields and
+    28 couplings (SIMT FP32 or FP64). One step = the checkpointed forward run
+    plus the adjoint sweep (device), timed with CUDA events; the plain forward
+    run (aqt_run) of the same trajectories is timed beside it, and the host's
+    FP64 contraction (aqt_grad_get) separately with the wall clock."""
+    import torch
+
+    from paper_1710_03431_gb300 import aqt as A
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if args.steps is None:
+        args.steps = 3
+    inst = workload(args)
+    prec = {"fp32": A.AQT_PREC_FP32, "fp64": A.AQT_PREC_FP64}[args.precision]
+    S = A.Session(inst, precision=prec, device=local, seed=rank_seed(inst.seed, rank))
+    t0 = time.perf_counter()
+    S.build()
+    table_s = time.perf_counter() - t0
+    S.grad_allocate(64)
+    stream = torch.cuda.current_stream()
+    P = A.aqt_grad_n_params(S.ctx)
+
+    def fwd():
+        A.aqt_run(S.ctx, stream.cuda_stream)
+
+    def grad_device():
+        A.aqt_grad_forward(S.ctx, stream.cuda_stream)
+        A.aqt_grad_backward(S.ctx, float("nan"), stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        fwd()
+        grad_device()
+        A.aqt_grad_get(S.ctx, P)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    fwd_ms = timed(fwd)
+    grad_ms = timed(grad_device)
+    ck = clocks.stop()
+    t1 = time.perf_counter()
+    g, value = A.aqt_grad_get(S.ctx, P)
+    host_s = time.perf_counter() - t1
+    if world > 1:
+        grad_ms = max_over_ranks(grad_ms, torch.device(f"cuda:{local}"))
+        fwd_ms = max_over_ranks(fwd_ms, torch.device(f"cuda:{local}"))
+    K, M = inst.n_grid, S.M
+    traj_steps = M * (K - 1)
+    S.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "gradient trajectory-steps/s (checkpointed forward + adjoint sweep)",
+        "value": world * traj_steps / (grad_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": grad_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {A.AQT_PREC_FP32: "f32", A.AQT_PREC_FP64: "f64"}[prec], "data": "synthetic",
+        "config": {"workload": f"tfim-8q-N256-M{M}-grid{K}-tf{inst.t_f:g}ns-{len(inst.sched_s)}knots-grad",
+                   "N": 1 << inst.n_qubits, "M": M, "n_grid": K, "params": P, "checkpoint_every": 64,
+                   "precision": args.precision, "parallelism": f"trajectories x{world}"},
+        "forward_ms": fwd_ms, "grad_over_forward": grad_ms / fwd_ms,
+        "host_contraction_s": host_s,
+        "grad_plus_host_over_forward": (grad_ms / 1e3 + host_s) / (fwd_ms / 1e3),
+        "p_gs_final": value, "grad_norm": float(np.sqrt(np.nansum(np.asarray(g) ** 2))),
+        "undefined_params": int(np.isnan(g).sum()),
+        "clocks": ck, "table_build_s": table_s, "gpu_launches": args.steps * (2 + 2 + 3 * ((K + 63) // 64)),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batch":
         run_batch(args)
+    elif args.config == "grad":
+        run_grad(args)
     else:
         run_ours(args)
 

@@ -343,6 +343,75 @@ aqt_status aqt_batch_sync(aqt_batch *batch, int32_t *member_status);
  * (SIMT) or 128-level blocks (tensor cores); tiles). */
 aqt_status aqt_batch_get_shape(aqt_batch *batch, int member, int32_t *shape);
 
+/* ---- Gradients (the paper has no derivatives; this extends its method) ----
+ *
+ * d<P>/dtheta of the trajectory average of the ground-manifold population of
+ * H_S(1), <P>, for the parameters theta, in this order: A(s) at the schedule
+ * knots, B(s) at the knots, hz_i (i = 0..n-1), Jzz_ij (i < j, row by row); there
+ * are 2 n_knots + n + n (n - 1) / 2 of them (aqt_grad_n_params).
+ *
+ * Estimator: a trajectory's record (jump times and channels) has probability
+ * density |psi~_T|^2, the squared norm of its unnormalised final state (the
+ * waiting-time density of Sec. IV / App. C times the channel probability
+ * Pi_i of App. B.1, Eq. Pi(t), is |A_i psi~|^2), so <P> is the integral over
+ * records of <psi~_T|P|psi~_T> and, with the record held fixed,
+ *   d<P>/dtheta = E[ dp/dtheta + (p - b) d log|psi~_T|^2 / dtheta ],
+ * p the final population of the normalised state, b any constant (the
+ * score d log|psi~_T|^2 has mean zero; b near <P> lowers the variance). The
+ * first term is the pathwise derivative through the no-jump propagation
+ * between jumps, the frame rotations and the jump operators at fixed jump
+ * times; the second is the score of the waiting times and of the channel
+ * choice. The device computes it by an adjoint sweep (backward through every
+ * trajectory, recomputed segment by segment from checkpoints written by a
+ * forward run every checkpoint_every grid points); the host (FP64) contracts
+ * the adjoint's per-grid-point sums with the derivatives of the instantaneous
+ * eigensystem (first-order perturbation theory), of gamma and S, and of the
+ * jump operators.
+ *
+ * Scope: AQT_PREC_FP64 or AQT_PREC_FP32, AQT_JUMP_REFINED, every level kept
+ * (no aqt_set_levels), at most 9 qubits; otherwise AQT_EINVAL. A parameter
+ * whose dH_S/dtheta couples two levels of one degenerate manifold at some
+ * grid point (at s = 0 of the transverse-field model: B at the first knot)
+ * has no derivative in the secular AME (the Bohr classes of Eq. Lindblad2
+ * regroup as the degeneracy lifts): its entry is NaN. */
+aqt_status aqt_grad_n_params(aqt_ctx *ctx, int *n_params);
+
+/* Device bytes of a gradient run for the current inputs (a second workspace,
+ * beside aqt_workspace_size's): checkpoints every checkpoint_every grid points
+ * ([n_grid / checkpoint_every] x M x N states), one segment's states and
+ * adjoints (4 x checkpoint_every x M x N), the per-grid-point sums
+ * (n_grid x N x N FP64) and room for jump_capacity jumps of the whole run
+ * (2 x N FP64 vectors each). Builds the host tables if needed. */
+aqt_status aqt_grad_workspace_size(aqt_ctx *ctx, int checkpoint_every, int64_t jump_capacity, size_t *bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, at least
+ * aqt_grad_workspace_size bytes for the same checkpoint_every and
+ * jump_capacity) for gradient runs. It must stay allocated while the context
+ * uses it; the library never frees it. Changing any set_* input invalidates
+ * it (aqt_grad_run then returns AQT_EINVAL). */
+aqt_status aqt_grad_bind_workspace(aqt_ctx *ctx, int checkpoint_every, int64_t jump_capacity, void *dptr,
+                                   size_t bytes);
+
+/* Forward run with checkpoints: the same propagation as aqt_run (the
+ * observables, jumps and final states are readable afterwards, and aqt_sync
+ * waits for it), plus every trajectory's state every checkpoint_every grid
+ * points. Asynchronous on `stream`. Tables must be built on the device
+ * (aqt_build_tables). */
+aqt_status aqt_grad_forward(aqt_ctx *ctx, void *stream);
+
+/* Backward sweep after aqt_grad_forward, asynchronous on `stream` (the same
+ * stream, or one ordered after it). baseline: the constant b of the
+ * estimator; NaN takes the forward run's own mean of P at s = 1 (a bias of
+ * order 1/M). */
+aqt_status aqt_grad_backward(aqt_ctx *ctx, double baseline, void *stream);
+
+/* Wait for the gradient run, then contract on the host: grad[n_params] gets
+ * d<P>/dtheta (NaN where undefined, see above), *value (may be NULL) the run's
+ * mean of P at s = 1. Errors: AQT_ENUMERIC; AQT_EOVERFLOW when a trajectory
+ * jumped more than 16 times inside one checkpoint segment (use a smaller
+ * checkpoint_every) or the run had more jumps than jump_capacity. */
+aqt_status aqt_grad_get(aqt_ctx *ctx, double *grad, int n_params, double *value);
+
 /* Table inspection (tests). N: the levels carried (aqt_set_levels), D = 2^n.
  * which: 0 eigenvalues [N]; 1 diag of H_eff,
  * [N][2] (re, im); 2 stage-one rates G[n][N]; 3 jump amplitudes

@@ -28,7 +28,8 @@ EXPORTS = ["aqt_create", "aqt_destroy", "aqt_last_error", "aqt_set_ising", "aqt_
            "aqt_get_observable_sums", "aqt_observables_from_sums", "aqt_get_rotation_error", "aqt_get_leakage", "aqt_get_jumps", "aqt_get_final_state", "aqt_debug_table",
            "aqt_run_static_scratch", "aqt_batch_create", "aqt_batch_destroy", "aqt_batch_last_error",
            "aqt_batch_workspace_size", "aqt_batch_bind_workspace", "aqt_batch_tune", "aqt_batch_run", "aqt_batch_sync",
-           "aqt_batch_get_shape"]
+           "aqt_batch_get_shape", "aqt_grad_n_params", "aqt_grad_workspace_size", "aqt_grad_bind_workspace",
+           "aqt_grad_forward", "aqt_grad_backward", "aqt_grad_get"]
 
 
 class aqt_jump(C.Structure):
@@ -92,6 +93,12 @@ def lib():
             "aqt_batch_run": (I, [P, P]),
             "aqt_batch_sync": (I, [P, C.POINTER(C.c_int32)]),
             "aqt_batch_get_shape": (I, [P, I, C.POINTER(C.c_int32)]),
+            "aqt_grad_n_params": (I, [P, C.POINTER(I)]),
+            "aqt_grad_workspace_size": (I, [P, I, I64, C.POINTER(SZ)]),
+            "aqt_grad_bind_workspace": (I, [P, I, I64, P, SZ]),
+            "aqt_grad_forward": (I, [P, P]),
+            "aqt_grad_backward": (I, [P, C.c_double, P]),
+            "aqt_grad_get": (I, [P, D, I, D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -320,6 +327,38 @@ def aqt_batch_get_shape(b, member: int):
     return tuple(int(x) for x in out)
 
 
+def aqt_grad_n_params(ctx) -> int:
+    n = C.c_int()
+    _check(ctx, lib().aqt_grad_n_params(ctx, C.byref(n)))
+    return n.value
+
+
+def aqt_grad_workspace_size(ctx, checkpoint_every: int, jump_capacity: int) -> int:
+    n = C.c_size_t()
+    _check(ctx, lib().aqt_grad_workspace_size(ctx, int(checkpoint_every), int(jump_capacity), C.byref(n)))
+    return n.value
+
+
+def aqt_grad_bind_workspace(ctx, checkpoint_every: int, jump_capacity: int, dptr: int, nbytes: int):
+    _check(ctx, lib().aqt_grad_bind_workspace(ctx, int(checkpoint_every), int(jump_capacity), C.c_void_p(dptr),
+                                              nbytes))
+
+
+def aqt_grad_forward(ctx, stream: int = 0):
+    _check(ctx, lib().aqt_grad_forward(ctx, C.c_void_p(stream)))
+
+
+def aqt_grad_backward(ctx, baseline: float = float("nan"), stream: int = 0):
+    _check(ctx, lib().aqt_grad_backward(ctx, float(baseline), C.c_void_p(stream)))
+
+
+def aqt_grad_get(ctx, n_params: int):
+    g = np.empty(n_params)
+    v = C.c_double()
+    _check(ctx, lib().aqt_grad_get(ctx, _dp(g), int(n_params), C.byref(v)))
+    return g, v.value
+
+
 # ---- convenience ------------------------------------------------------------------
 class Session:
     """One context configured from an instance (see ``workloads.Instance``),
@@ -376,6 +415,23 @@ class Session:
 
     def final_state(self, basis=1):
         return aqt_get_final_state(self.ctx, basis, self.M, self.D if basis == 1 else self.N)
+
+    def grad_allocate(self, checkpoint_every=64, jump_capacity=None):
+        """Bind a gradient workspace (torch uint8 tensor on the context's device)."""
+        import torch
+        jc = int(jump_capacity if jump_capacity is not None else max(1024, 4 * self.M))
+        nbytes = aqt_grad_workspace_size(self.ctx, checkpoint_every, jc)
+        if getattr(self, "gws", None) is None or self.gws.numel() < nbytes:
+            self.gws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        aqt_grad_bind_workspace(self.ctx, checkpoint_every, jc, self.gws.data_ptr(), self.gws.numel())
+
+    def gradient(self, baseline=float("nan"), checkpoint_every=64, jump_capacity=None):
+        """Forward run with checkpoints and the adjoint sweep; returns
+        (d<P>/dtheta, <P>) for P the ground-manifold population at s = 1."""
+        self.grad_allocate(checkpoint_every, jump_capacity)
+        aqt_grad_forward(self.ctx, self.stream())
+        aqt_grad_backward(self.ctx, baseline, self.stream())
+        return aqt_grad_get(self.ctx, aqt_grad_n_params(self.ctx))
 
     def close(self):
         if self.ctx:

@@ -15,9 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaqt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cpp", "batch.cpp", "tables.cpp", "lanczos.cpp", "eigen.cpp", "bath.cpp", "propagate.cu", "propagate_f32.cu",
-           "propagate_f64.cu", "propagate_batch_f32.cu", "propagate_batch_f64.cu", "propagate_tc.cu",
-           "static_scratch.cu"]
+SOURCES = ["capi.cpp", "batch.cpp", "grad.cpp", "tables.cpp", "lanczos.cpp", "eigen.cpp", "bath.cpp", "propagate.cu",
+           "propagate_f32.cu", "propagate_f64.cu", "propagate_batch_f32.cu", "propagate_batch_f64.cu", "propagate_tc.cu",
+           "adjoint_f32.cu", "adjoint_f64.cu", "static_scratch.cu"]
 
 
 def nvcc() -> str:

@@ -28,6 +28,10 @@ struct Bath {
     double lamb_direct(double w) const;
     double lamb(double w) const;
     void build_lamb(double wmax);
+    // derivatives in w: of gamma in closed form (w != 0), of the tabulated S by
+    // a central difference of the interpolant
+    double gamma_deriv(double w) const;
+    double lamb_deriv(double w) const;
 };
 
 bool sym_eigen(int n, double *A, double *evals, double *V);
@@ -139,6 +143,13 @@ struct Inputs {
 // Returns AQT_OK or an error with a message in *err.
 aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err);
 
+// out[i*ld + j] = sum_k X[i][k] Y[j][k] (rows of length len, row-major).
+void gram_rows(const double *X, const double *Y, int ni, int nj, int len, double *out, int ld);
+// M_alpha = V_g^T sz_alpha V_g for every qubit, out[alpha][a][b], from the tables' eigenvectors.
+void sz_frames_at(const Tables &tab, int g, double *M);
+// A(s), B(s) of the piecewise-linear schedule.
+void schedule_value(const Inputs &in, double s, double *A, double *B);
+
 // Jump amplitudes R_alpha[a][b] = sqrt(gamma(w_ab)) M_alpha[a][b] of grid point
 // g, out[alpha][a][b], recomputed from the tables' eigenvectors (inspection).
 void jump_amplitudes(const Inputs &in, const Tables &tab, int g, double *out);
@@ -164,6 +175,63 @@ struct DevTables {
 // (FIXED: a jump test with probability tau lambda at the start of each
 // half-step).
 enum JumpTiming : int { kTimingRefined = 0, kTimingGrid = 1, kTimingFixed = 2 };
+
+// One jump of a segment recompute of a gradient run, kept for the backward
+// sweep: where it happened (grid point, half-step, time after the half-step's
+// start), its channel (qubit, source and target levels as draw_apply returns
+// them) and whether the grid point used the general routine.
+struct AdjJump {
+    int32_t g, half, alpha, bsrc, adst, general;
+    double t_rel;
+};
+
+// Gradient runs only (all pointers null otherwise). The forward run writes a
+// checkpoint of every trajectory at the end of grid point ckpt_every*j - 1
+// (j = 1, 2, ...): its state, clock, log threshold and jump count. A segment
+// recompute restarts from checkpoint g_begin / ckpt_every (or the initial
+// state), runs grid points g_begin .. g_end and writes, per grid point and
+// trajectory, the normalised state at the start of the grid point's frozen
+// span (after the frame rotation into it) and at its end, the norm of the
+// rotated state, and its jumps.
+struct AdjParams {
+    void *ckpt;          // [n_ckpt][M][N][2] state precision
+    double *ckpt_clock;  // [n_ckpt][M][2]: ell, log r
+    int32_t *ckpt_nj;    // [n_ckpt][M]
+    int ckpt_every;
+    int g_begin, g_end;
+    void *seg_c;         // [g - g_begin][2: start, end][M][N][2] state precision
+    double *seg_nrot;    // [g - g_begin][M]
+    AdjJump *jrec;       // [M][slots]
+    double *jvec;        // [M][slots][2][N][2]: normalised state before and after the jump (FP64)
+    int32_t *jn;         // [M] jumps of the segment so far
+    int slots;
+};
+
+// One compact record of a jump for the host: where and which channel, then
+// (in jump_vec) the normalised state before the jump and the adjoint after it.
+struct AdjJumpOut {
+    AdjJump r;
+    int64_t traj;
+};
+
+struct AdjBack {
+    const void *seg_c;       // [g - g_begin][2][M][N][2] state precision: c_s, c_e
+    const double *seg_nrot;  // [g - g_begin][M]
+    void *seg_mu;            // [g - g_begin][2][M][N][2]: mu_s, mu_e (written)
+    void *carry;             // [M][N][2]: adjoint at the end of g_end (read), of g_begin - 1 (written)
+    double *lev;             // [K][N][2] trajectory sums of 2 l (Im, Re)(mu_a^* c_a) (atomics)
+    const AdjJump *jrec;     // [M][slots]
+    const double *jvec;      // [M][slots][2][N][2]
+    const int32_t *jn;       // [M]
+    AdjJumpOut *jout;           // [jcap] compact jump list for the host
+    double *jout_vec;        // [jcap][2][N][2]: state before, adjoint after (FP64)
+    unsigned long long *jout_n;
+    int64_t jout_cap;
+    double *wscr;            // [n_cta][8 warps][10 N] FP64 per-warp scratch (jumped spans)
+    double baseline;         // b; NaN: the run's mean of P at s = 1
+    int g_begin, g_end, slots;
+    int32_t *status;
+};
 
 struct RunParams {
     int n, N, K, TT, RA, n_cta;
@@ -193,6 +261,7 @@ struct RunParams {
     // trajectories and steps, as the bits of a non-negative float (atomicMax on
     // the bits orders like the values); not recorded when null.
     unsigned int *norm_err;
+    AdjParams adj;
 };
 
 // Jump scratch per warp (SIMT) or jump slot (tensor-core path), in double2
@@ -214,6 +283,17 @@ inline size_t scratch_bytes(int n_cta, int N, int TT, bool tensor_core) {
 // reduction on `stream`. Returns a CUDA error code (0 on success).
 int launch_run(const RunParams &p, int precision, void *stream, size_t smem_bytes);
 int launch_simt_f32(const RunParams &p, void *stream, size_t smem);
+// Gradient runs: one segment of the backward sweep (adjoint.cuh), the
+// per-grid-point outer products X_g of a segment, and the backward tile's
+// shared memory.
+int launch_adjoint_f32(const RunParams &p, const AdjBack &b, void *stream, size_t smem);
+int launch_adjoint_f64(const RunParams &p, const AdjBack &b, void *stream, size_t smem);
+int launch_xgemm_f32(const void *seg_c, const void *seg_mu, int64_t M, int N, int K, int g_begin, int n_g,
+                     double *xout, void *stream);
+int launch_xgemm_f64(const void *seg_c, const void *seg_mu, int64_t M, int N, int K, int g_begin, int n_g,
+                     double *xout, void *stream);
+size_t adjoint_smem_bytes_f32(int N, int TT);
+size_t adjoint_smem_bytes_f64(int N, int TT);
 int launch_simt_f64(const RunParams &p, void *stream, size_t smem);
 
 // ---------------------------------------------------------- batches ---------
@@ -258,6 +338,25 @@ constexpr size_t kSimtSmemLimit = 200 * 1024;
 // pointing at the context's device tables (outputs and scratch left unset),
 // the precision and the kernel's dynamic shared memory.
 aqt_status static_scratch_need(aqt_ctx *ctx, size_t *bytes);
+
+// Gradient runs (grad.cpp): the context's inputs, host tables and launch
+// shape, and (need_device_tables) its run parameters over the device tables;
+// the gradient state the context owns; marking the context's run as done on
+// `stream` (for aqt_sync and the getters).
+struct GradState;
+void grad_free(GradState *g);
+struct GradAccess {
+    RunParams p;
+    const Inputs *in = nullptr;
+    const Tables *tab = nullptr;
+    int TT = 0, RA = 0, n_cta = 0;
+    size_t smem = 0;
+    uint64_t version = 0;
+};
+aqt_status grad_access(aqt_ctx *ctx, GradAccess *a, bool need_device_tables);
+GradState *grad_state_get(aqt_ctx *ctx);
+void grad_state_set(aqt_ctx *ctx, GradState *g);
+void grad_mark_ran(aqt_ctx *ctx, void *stream);
 aqt_status static_run_params(aqt_ctx *ctx, RunParams *p);
 
 // A context as a member of a batch: its run parameters over its device tables

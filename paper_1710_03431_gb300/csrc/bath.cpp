@@ -28,6 +28,35 @@ double Bath::gamma(double w) const {
     return 2.0 * M_PI * eta_g2 * w * std::exp(-std::fabs(w) / omega_c) / den;
 }
 
+// d gamma / dw for w != 0: gamma = 2 pi eta_g2 q(w) e^{-|w|/w_c} with
+// q(w) = w / (1 - e^{-beta w}); q'(w) = (1 - e^{-x} (1 + x)) / (1 - e^{-x})^2,
+// x = beta w, written for x < 0 as e^x (e^x - 1 - x) / (e^x - 1)^2 so that
+// neither form overflows, and as its Taylor series 1/2 + x/6 - x^3/180 for
+// |x| < 1e-4 (where the closed form cancels).
+double Bath::gamma_deriv(double w) const {
+    const double x = beta * w;
+    double dq;
+    if (std::fabs(x) < 1e-4) {
+        dq = 0.5 + x / 6.0 - x * x * x / 180.0;  // series of d/dx [x / (1 - e^{-x})]
+    } else if (x >= 0.0) {
+        const double em = -std::expm1(-x);  // 1 - e^{-x}
+        dq = (em - x * std::exp(-x)) / (em * em);
+    } else {
+        const double ep = std::expm1(x);  // e^x - 1
+        dq = std::exp(x) * (ep - x) / (ep * ep);
+    }
+    const double q = w / (-std::expm1(-x));
+    const double e = std::exp(-std::fabs(w) / omega_c);
+    const double sgn = w > 0.0 ? 1.0 : -1.0;
+    return 2.0 * M_PI * eta_g2 * e * (dq - sgn * q / omega_c);
+}
+
+double Bath::lamb_deriv(double w) const {
+    if (!lamb_shift) return 0.0;
+    const double h = 1e-5 * std::max(1.0, std::fabs(w));
+    return (lamb(w + h) - lamb(w - h)) / (2.0 * h);
+}
+
 namespace {
 
 // 15-point Gauss-Legendre nodes/weights on [-1, 1], computed by Newton

@@ -39,6 +39,8 @@ struct aqt_ctx {
     long long wait_polls = kDefaultWaitPolls;
     size_t uploaded = 0;  // bytes copied to the device by the last aqt_build_tables
     uint64_t version = 0;  // changes whenever the device tables or the workspace stop being valid
+    GradState *grad = nullptr;  // gradient-run workspace and state (grad.cpp)
+    ~aqt_ctx() { grad_free(grad); }
 };
 
 namespace {
@@ -270,6 +272,41 @@ aqt_status batch_member(aqt_ctx *c, BatchMember *m) {
 uint64_t ctx_version(const aqt_ctx *c) { return c->version; }
 
 void batch_member_ran(aqt_ctx *c, void *stream) {
+    c->stream = (cudaStream_t)stream;
+    c->ran = true;
+}
+
+aqt_status grad_access(aqt_ctx *c, GradAccess *a, bool need_device_tables) {
+    if (!inputs_complete(c)) return fail(c, AQT_EINVAL, "set all inputs first");
+    aqt_status s = device_shape_check(c);
+    if (s == AQT_OK) s = use_device(c);
+    if (s != AQT_OK) return s;
+    if (need_device_tables) {
+        if (!c->tables_on_device) return fail(c, AQT_EINVAL, "build tables on the device before running");
+        fill_params(c, &a->p);
+    } else {
+        if ((s = ensure_host_tables(c)) != AQT_OK) return s;
+        compute_layout(c);
+        a->p = RunParams{};
+    }
+    a->in = &c->in;
+    a->tab = &c->tab;
+    a->TT = c->TT;
+    a->RA = c->RA;
+    a->n_cta = c->n_cta;
+    a->smem = c->smem;
+    a->version = c->version;
+    return AQT_OK;
+}
+
+GradState *grad_state_get(aqt_ctx *c) { return c->grad; }
+
+void grad_state_set(aqt_ctx *c, GradState *g) {
+    grad_free(c->grad);
+    c->grad = g;
+}
+
+void grad_mark_ran(aqt_ctx *c, void *stream) {
     c->stream = (cudaStream_t)stream;
     c->ran = true;
 }

@@ -46,7 +46,7 @@ namespace dev {
 
 constexpr int kMaxJumpsPerHalf = 64;
 constexpr int kMaxAlpha = 16;
-enum : int32_t { kStatusNumeric = 2, kStatusTimeout = 4 };
+enum : int32_t { kStatusNumeric = 2, kStatusTimeout = 4, kStatusAdjSlots = 8 };
 
 template <typename T>
 static __device__ __forceinline__ T warp_sum(T v) {
@@ -715,11 +715,53 @@ static __device__ __forceinline__ void jump_half_step(const RunParams &p, int g,
         ++nj;
         const Philox4 rnd = traj_event(p.seed, traj, nj);
         const double u1 = uniform01(rnd.x[0]), u2 = uniform01(rnd.x[1]), u3 = uniform01(rnd.x[2]);
+        // segment recompute of a gradient run: keep the states around the jump
+        int aslot = -1;
+        if (p.adj.jrec) {
+            aslot = __shfl_sync(0xffffffffu, lane == 0 ? p.adj.jn[traj] : 0, 0);
+            if (aslot < p.adj.slots) {
+                double *v = p.adj.jvec + ((size_t)traj * p.adj.slots + aslot) * 4 * N;
+#pragma unroll
+                for (int j = 0; j < NPL; ++j) {
+                    const int a = 32 * j + lane;
+                    if (a < N) {
+                        v[2 * a] = (double)cr[j];
+                        v[2 * a + 1] = (double)ci[j];
+                    }
+                }
+            } else if (lane == 0) {
+                atomicOr(p.status, kStatusAdjSlots);
+            }
+        }
         int bsrc = -1, adst = -1;
         const int al = draw_apply<T, NPL>(p, g, cr, ci, u1, u2, lane, slow, &bsrc, &adst);
         if (al < 0) {
             ok = false;
             break;
+        }
+        if (aslot >= 0 && aslot < p.adj.slots) {
+            double *v = p.adj.jvec + (((size_t)traj * p.adj.slots + aslot) * 2 + 1) * 2 * N;
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                const int a = 32 * j + lane;
+                if (a < N) {
+                    v[2 * a] = (double)cr[j];
+                    v[2 * a + 1] = (double)ci[j];
+                }
+            }
+            if (lane == 0) {
+                const GridMeta meta = p.tab.meta[g];
+                AdjJump r;
+                r.g = g;
+                r.half = half;
+                r.alpha = al;
+                r.bsrc = bsrc;
+                r.adst = adst;
+                r.general = !(meta.simple && !meta.degenerate);
+                r.t_rel = (p.tau - tau_rem) + t;
+                p.adj.jrec[(size_t)traj * p.adj.slots + aslot] = r;
+                p.adj.jn[traj] = aslot + 1;
+            }
         }
         record_jump(p, traj, g, half, al, bsrc, adst, t_half0 + (p.tau - tau_rem) + t, lane);
         __syncwarp();

@@ -171,18 +171,89 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
     static_assert(kWarps <= kScratchSlots, "one jump scratch slot per warp");
     double2 *c64 = scr + (size_t)warp * kSlotDouble2 * N;
 
-    // initial state: ground state of H_S(0) (level 0), threshold from event 0
-    for (int i = tid; i < N * LD; i += kThreads) {
-        const int a = i / LD, t = i % LD;
-        cre[i] = (a == 0 && t < TT && t0 + t < p.M) ? (R)1 : (R)0;
-        cim[i] = (R)0;
+    // Gradient runs: a segment recompute (seg) restarts from a checkpoint and
+    // runs grid points g_begin .. g_end only; a checkpointed forward run (ckpt)
+    // writes the checkpoints on the way.
+    const AdjParams &adj = p.adj;
+    const bool seg = adj.seg_c != nullptr;
+    const bool ckpt = !seg && adj.ckpt != nullptr;
+    const int g_begin = seg ? adj.g_begin : 0, g_end = seg ? adj.g_end : K - 1;
+    if (seg && g_begin > 0) {
+        // restart from checkpoint g_begin / ckpt_every: the state at the end of grid point g_begin - 1
+        const size_t j = (size_t)(g_begin / adj.ckpt_every - 1);
+        const R *cs = reinterpret_cast<const R *>(adj.ckpt);
+        for (int i = tid; i < N * LD; i += kThreads) {
+            const int t = i / N, a = i % N;
+            if (t >= LD) continue;
+            const bool v = t < TT && t0 + t < p.M;
+            const size_t o = ((j * p.M + t0 + t) * N + a) * 2;
+            cre[a * LD + t] = v ? cs[o] : (R)0;
+            cim[a * LD + t] = v ? cs[o + 1] : (R)0;
+        }
+        for (int t = tid; t < TT; t += kThreads) {
+            const bool v = t0 + t < p.M;
+            const size_t o = j * p.M + t0 + t;
+            ell[t] = v ? adj.ckpt_clock[2 * o] : 0.0;
+            logr[t] = v ? adj.ckpt_clock[2 * o + 1] : 0.0;
+            nj[t] = v ? adj.ckpt_nj[o] : 0;
+            leak[t] = 0.0;
+        }
+    } else {
+        // initial state: ground state of H_S(0) (level 0), threshold from event 0
+        for (int i = tid; i < N * LD; i += kThreads) {
+            const int a = i / LD, t = i % LD;
+            cre[i] = (a == 0 && t < TT && t0 + t < p.M) ? (R)1 : (R)0;
+            cim[i] = (R)0;
+        }
+        for (int t = tid; t < TT; t += kThreads) {
+            ell[t] = 0.0;
+            leak[t] = 0.0;
+            nj[t] = 0;
+            logr[t] = (t0 + t < p.M) ? log(uniform01(traj_event(p.seed, t0 + t, 0).x[0])) : 0.0;
+        }
     }
-    for (int t = tid; t < TT; t += kThreads) {
-        ell[t] = 0.0;
-        leak[t] = 0.0;
-        nj[t] = 0;
-        logr[t] = (t0 + t < p.M) ? log(uniform01(traj_event(p.seed, t0 + t, 0).x[0])) : 0.0;
-    }
+    // segment recompute: normalised state of every trajectory at the start (e = 0)
+    // or end (e = 1) of grid point g's frozen span, and the rotated state's norm
+    auto seg_store = [&](int g, int e, bool normalise) {
+        R *dst = reinterpret_cast<R *>(adj.seg_c) + (size_t)((g - g_begin) * 2 + e) * p.M * N * 2;
+        for (int t = warp; t < TT; t += kWarps) {
+            if (t0 + t >= p.M) continue;
+            R sc = (R)1;
+            if (normalise) {
+                double nu = 0.0;
+                for (int a = lane; a < N; a += 32) {
+                    const double re = cre[a * LD + t], im = cim[a * LD + t];
+                    nu += re * re + im * im;
+                }
+                nu = warp_sum(nu);
+                sc = (R)(1.0 / sqrt(nu));
+                if (lane == 0) adj.seg_nrot[(size_t)(g - g_begin) * p.M + t0 + t] = sqrt(nu);
+            }
+            R *q = dst + (size_t)(t0 + t) * N * 2;
+            for (int a = lane; a < N; a += 32) {
+                q[2 * a] = cre[a * LD + t] * sc;
+                q[2 * a + 1] = cim[a * LD + t] * sc;
+            }
+        }
+    };
+    auto ckpt_store = [&](int g) {
+        const size_t j = (size_t)((g + 1) / adj.ckpt_every - 1);
+        R *cs = reinterpret_cast<R *>(adj.ckpt);
+        for (int t = warp; t < TT; t += kWarps) {
+            if (t0 + t >= p.M) continue;
+            R *q = cs + ((j * p.M + t0 + t) * N) * 2;
+            for (int a = lane; a < N; a += 32) {
+                q[2 * a] = cre[a * LD + t];
+                q[2 * a + 1] = cim[a * LD + t];
+            }
+            if (lane == 0) {
+                const size_t o = j * p.M + t0 + t;
+                adj.ckpt_clock[2 * o] = ell[t];
+                adj.ckpt_clock[2 * o + 1] = logr[t];
+                adj.ckpt_nj[o] = nj[t];
+            }
+        }
+    };
     const R *eh_tab = ehalf_table<R>(p);
     auto load_grid = [&](int g) {
         for (int a = tid; a < N; a += kThreads) {
@@ -234,13 +305,23 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
         }
     };
 
-    load_grid(0);
-    __syncthreads();
-    observe(0, gs0);
-    half_all(0, 1);
+    if (g_begin == 0) {
+        load_grid(0);
+        __syncthreads();
+        if (!seg) observe(0, gs0);
+        half_all(0, 1);
+        if (seg) {
+            __syncthreads();
+            seg_store(0, 1, false);
+        }
+        if (ckpt && adj.ckpt_every == 1 && K > 1) {
+            __syncthreads();
+            ckpt_store(0);
+        }
+    }
 
     const int tx = tid % TXN, ty = tid / TXN;
-    for (int g = 1; g < K; ++g) {
+    for (int g = max(g_begin, 1); g <= g_end; ++g) {
         // ---- rotation c <- O_{g-1} c ---------------------------------------------
         R accr[RA][4], acci[RA][4];
 #pragma unroll
@@ -282,12 +363,24 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
         }
         load_grid(g);
         __syncthreads();
+        if (seg) {
+            seg_store(g, 0, true);
+            __syncthreads();
+        }
         // ---- epilogue: half-step into s_g, observe, half-step out of s_g ------------
         half_all(g, 0);
         __syncthreads();
-        observe(g, p.tab.meta[g].gs_size);
+        if (!seg) observe(g, p.tab.meta[g].gs_size);
         if (g < K - 1) half_all(g, 1);
+        if (seg) {
+            __syncthreads();
+            seg_store(g, 1, false);
+        } else if (ckpt && g < K - 1 && (g + 1) % adj.ckpt_every == 0) {
+            __syncthreads();
+            ckpt_store(g);
+        }
     }
+    if (seg) return;
     if (p.norm_err && lane == 0) atomicMax(p.norm_err, __float_as_uint(nerr));
     __syncthreads();
     for (int i = tid; i < N * TT; i += kThreads) {

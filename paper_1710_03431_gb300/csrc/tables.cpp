@@ -580,4 +580,15 @@ void jump_amplitudes(const Inputs &in, const Tables &tab, int g, double *out) {
         }
 }
 
+// Exported helpers of the gradient contraction (grad.cpp).
+void gram_rows(const double *X, const double *Y, int ni, int nj, int len, double *out, int ld) {
+    gram(X, Y, ni, nj, len, out, ld, false);
+}
+
+void sz_frames_at(const Tables &tab, int g, double *M) {
+    frames_of(tab, &tab.V[(size_t)g * tab.D * tab.N], M);
+}
+
+void schedule_value(const Inputs &in, double s, double *A, double *B) { schedule_at(in, s, A, B); }
+
 }  // namespace aqt

@@ -156,3 +156,19 @@ def cfg_batch(n_instances: int = 64, qubits=(6, 7, 8), M: int = 2048, n_grid: in
         out.append(tfim_instance(n, 1710_03500 + i, **base))
     return out
 
+
+
+def cfg_grad(n_knots: int = 8, **kw) -> Instance:
+    """Differentiation workload: the 8-qubit complete-graph instance of
+    ``cfg_main`` (N = 256) with its linear schedule written as n_knots
+    piecewise-linear control points s_k = k / (n_knots - 1) of A and B, t_f =
+    10 ns, 2000-point grid, M = 2^14 trajectories. Parameters: the 2 n_knots
+    control values, the 8 fields and the 28 couplings."""
+    base = dict(t_f=10.0, n_grid=2000, M=1 << 14, seed=1710_03433)
+    base.update(kw)
+    inst = tfim_instance(8, 1710_03432, **base)
+    s = np.linspace(0.0, 1.0, n_knots)
+    inst.sched_s = s
+    inst.sched_A = 2.0 * math.pi * (1.0 - s)
+    inst.sched_B = 2.0 * math.pi * s
+    return inst
