@@ -65,7 +65,7 @@ def parse():
     if a.M is None:
         a.M = {"main": 10_000, "small": 1000, "batch": 2048, "grad": 1 << 14}[a.config]
     if a.n_grid is None:
-        a.n_grid = 2000 if a.config == "main" else 1000
+        a.n_grid = 2000 if a.config in ("main", "grad") else 1000
     if a.tf is None:
         a.tf = 20.0 if a.config == "batch" else 10.0
     return a

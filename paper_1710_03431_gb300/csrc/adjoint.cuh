@@ -288,6 +288,17 @@ static __device__ __forceinline__ void span_with_jumps_any(const RunParams &p, c
     else span_with_jumps<16>(p, b, g, traj, c_s, c_e, mu, lsum, k_lo, k_hi, scr, lane);
 }
 
+// Four consecutive entries of a 16-byte aligned tile row.
+static __device__ __forceinline__ void load4(const float *p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+static __device__ __forceinline__ void load4(const double *p, double v[4]) {
+    const double2 q0 = *reinterpret_cast<const double2 *>(p);
+    const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
 // Shared memory of the backward tile (bytes).
 inline size_t back_smem_bytes(int N, int TT, size_t rs) {
     const int LD = TT + 4;
@@ -452,11 +463,8 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
             __syncthreads();
             for (int aa = 0; aa < KB; ++aa) {
                 R vr[4], vi[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    vr[j] = mre[(a0 + aa) * LD + 4 * tx + j];
-                    vi[j] = mim[(a0 + aa) * LD + 4 * tx + j];
-                }
+                load4(&mre[(a0 + aa) * LD + 4 * tx], vr);
+                load4(&mim[(a0 + aa) * LD + 4 * tx], vi);
 #pragma unroll
                 for (int i = 0; i < RA; ++i) {
                     const int bo = ty + i * TYN;
@@ -499,7 +507,7 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
 }
 
 template <typename R, int RA>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     adjoint_segment(const __grid_constant__ RunParams p, const __grid_constant__ AdjBack b) {
     extern __shared__ __align__(16) unsigned char smem[];
     back_tile<R, RA>(p, b, blockIdx.x, smem);

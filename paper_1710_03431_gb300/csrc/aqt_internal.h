@@ -32,6 +32,8 @@ struct Bath {
     // a central difference of the interpolant
     double gamma_deriv(double w) const;
     double lamb_deriv(double w) const;
+    // gamma, gamma' (0 at w = 0), S and the derivative of its interpolant, in one call
+    void rates(double w, double *g, double *dg, double *s, double *ds) const;
 };
 
 bool sym_eigen(int n, double *A, double *evals, double *V);
@@ -120,6 +122,7 @@ struct Tables {
     // 1 / |H_eff|, |lambda / (lambda^2 - dlambda/dt)|.
     double dt_bound[3] = {0.0, 0.0, 0.0};
     int dt_bound_at[3] = {0, 0, 0};
+    Bath bath;  // the bath with the Lamb-shift table the tables were built with
 };
 
 struct Inputs {

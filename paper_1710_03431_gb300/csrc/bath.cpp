@@ -171,6 +171,35 @@ void Bath::build_lamb(double wmax) {
     for (auto &x : th) x.join();
 }
 
+void Bath::rates(double w, double *g, double *dg, double *s, double *ds) const {
+    *g = gamma(w);
+    *dg = w == 0.0 ? 0.0 : gamma_deriv(w);
+    *s = 0.0;
+    *ds = 0.0;
+    if (!lamb_shift) return;
+    for (const Zone &z : zones) {
+        if (std::fabs(w) > z.half) continue;
+        const double u = w / z.h;
+        const int k = (int)std::floor(u);
+        const double t = u - k;
+        const double *v = &z.val[k + z.n0 - 1];
+        // the Lagrange interpolant of lamb() and its derivative in t (nodes -1, 0, 1, 2)
+        const double l0 = -t * (t - 1.0) * (t - 2.0) / 6.0;
+        const double l1 = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+        const double l2 = -(t + 1.0) * t * (t - 2.0) / 2.0;
+        const double l3 = (t + 1.0) * t * (t - 1.0) / 6.0;
+        const double d0 = -(3.0 * t * t - 6.0 * t + 2.0) / 6.0;
+        const double d1 = (3.0 * t * t - 4.0 * t - 1.0) / 2.0;
+        const double d2 = -(3.0 * t * t - 2.0 * t - 2.0) / 2.0;
+        const double d3 = (3.0 * t * t - 1.0) / 6.0;
+        *s = l0 * v[0] + l1 * v[1] + l2 * v[2] + l3 * v[3];
+        *ds = (d0 * v[0] + d1 * v[1] + d2 * v[2] + d3 * v[3]) / z.h;
+        return;
+    }
+    *s = lamb_direct(w);
+    *ds = lamb_deriv(w);
+}
+
 double Bath::lamb(double w) const {
     if (!lamb_shift) return 0.0;
     for (const Zone &z : zones) {

@@ -128,6 +128,37 @@ struct Contract {
     std::vector<std::vector<size_t>> by_g;
 };
 
+// Two-lane FP64 vector (GCC vector extension: NEON on aarch64, SSE2 on x86-64).
+typedef double v2d __attribute__((vector_size(16), aligned(8)));
+
+// out[i*ld + j] = sum_k X[i][k] Y[j][k] (rows of length len, row-major): 4 x 4
+// register blocks, k in pairs on two-lane vectors (len even).
+void rows_dot(const double *X, const double *Y, int ni, int nj, int len, double *out, int ld) {
+    if (len % 2 || ni % 4 || nj % 4) {
+        gram_rows(X, Y, ni, nj, len, out, ld);
+        return;
+    }
+    for (int i0 = 0; i0 < ni; i0 += 4)
+        for (int j0 = 0; j0 < nj; j0 += 4) {
+            v2d acc[4][4];
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) acc[a][b] = v2d{0.0, 0.0};
+            const double *x = X + (size_t)i0 * len, *y = Y + (size_t)j0 * len;
+            for (int k = 0; k < len; k += 2) {
+                const v2d xa = *(const v2d *)(x + k), xb = *(const v2d *)(x + len + k);
+                const v2d xc = *(const v2d *)(x + 2 * len + k), xd = *(const v2d *)(x + 3 * len + k);
+                const v2d ya = *(const v2d *)(y + k), yb = *(const v2d *)(y + len + k);
+                const v2d yc = *(const v2d *)(y + 2 * len + k), yd = *(const v2d *)(y + 3 * len + k);
+                acc[0][0] += xa * ya; acc[0][1] += xa * yb; acc[0][2] += xa * yc; acc[0][3] += xa * yd;
+                acc[1][0] += xb * ya; acc[1][1] += xb * yb; acc[1][2] += xb * yc; acc[1][3] += xb * yd;
+                acc[2][0] += xc * ya; acc[2][1] += xc * yb; acc[2][2] += xc * yc; acc[2][3] += xc * yd;
+                acc[3][0] += xd * ya; acc[3][1] += xd * yb; acc[3][2] += xd * yc; acc[3][3] += xd * yd;
+            }
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) out[(size_t)(i0 + a) * ld + j0 + b] = acc[a][b][0] + acc[a][b][1];
+        }
+}
+
 // d/dw sqrt(gamma(w)) = gamma'(w) / (2 sqrt(gamma(w)))
 double dsqrt_gamma(const Bath &b, double w) { return b.gamma_deriv(w) / (2.0 * std::sqrt(b.gamma(w))); }
 
@@ -135,7 +166,7 @@ double dsqrt_gamma(const Bath &b, double w) { return b.gamma_deriv(w) / (2.0 * s
 void contract_point(const Contract &C, int g, std::vector<double> &grad, std::vector<char> &und) {
     const Inputs &in = C.in;
     const Tables &tab = C.tab;
-    const Bath &bath = in.bath;
+    const Bath &bath = tab.bath;  // with its Lamb-shift table (in.bath has none: S would be integrated per call)
     const int n = in.n, N = tab.N, D = tab.D, K = tab.K;
     const size_t NN = (size_t)N * N;
     const double *ev = &tab.evals[(size_t)g * N];
@@ -154,30 +185,35 @@ void contract_point(const Contract &C, int g, std::vector<double> &grad, std::ve
         for (int q = f; q < f + m; ++q) y[q] += v / m;
     };
     // ---- effective Hamiltonian diagonal K_bb -------------------------------------------
+    // coefficients per level pair (a <- b): cf = Re(kappa_b^* f(w)), cd = Re(kappa_b^* f'(w)),
+    // kappa^* = rho - i sig (rho, sig: the sums for d Re K_bb, d Im K_bb), f = S - (i/2) gamma
     const double *lv = &C.lev[(size_t)g * N * 2];
-    for (int b = 0; b < N; ++b) {
-        const double rho = lv[2 * b], sig = lv[2 * b + 1];  // coefficients of d Re K_bb, d Im K_bb
-        y[b] += rho;
-        if (rho == 0.0 && sig == 0.0) continue;
-        for (int a = 0; a < N; ++a) {
-            const double w = E[b] - E[a];
-            const bool zero = mfirst[a] == mfirst[b];  // same manifold: omega = 0 identically
-            const double lam = bath.lamb(w), gam = bath.gamma(w);
-            // Re(kappa^* f) with kappa^* = rho - i sig and f = S - (i/2) gamma
-            const double cf = rho * lam - 0.5 * sig * gam;
-            double m2 = 0.0;
-            for (int al = 0; al < n; ++al) {
-                const double m = Mall[(size_t)al * NN + (size_t)a * N + b];
-                m2 += m * m;
-                Y[(size_t)al * NN + (size_t)a * N + b] += 2.0 * cf * m;
-            }
-            if (!zero) {
-                const double cd = rho * bath.lamb_deriv(w) - 0.5 * sig * bath.gamma_deriv(w);
-                add_dE(b, cd * m2);
-                add_dE(a, -cd * m2);
-            }
+    std::vector<double> cf(NN), cd(NN, 0.0), m2(NN, 0.0);
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            const double rho = lv[2 * b], sig = lv[2 * b + 1];
+            double gam, dgam, lam, dlam;
+            bath.rates(E[b] - E[a], &gam, &dgam, &lam, &dlam);
+            cf[(size_t)a * N + b] = rho * lam - 0.5 * sig * gam;
+            if (mfirst[a] != mfirst[b]) cd[(size_t)a * N + b] = rho * dlam - 0.5 * sig * dgam;  // w = 0 identically otherwise
+        }
+    for (int b = 0; b < N; ++b) y[b] += lv[2 * b];
+    for (int al = 0; al < n; ++al) {
+        const double *Ma = &Mall[(size_t)al * NN];
+        double *Ya = &Y[(size_t)al * NN];
+        for (size_t i = 0; i < NN; ++i) {
+            Ya[i] += 2.0 * cf[i] * Ma[i];
+            m2[i] += Ma[i] * Ma[i];
         }
     }
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            const double v = cd[(size_t)a * N + b] * m2[(size_t)a * N + b];
+            if (v != 0.0) {
+                add_dE(b, v);
+                add_dE(a, -v);
+            }
+        }
     // ---- jumps at this grid point ---------------------------------------------------------
     for (size_t idx : C.by_g[g]) {
         const AdjJumpOut &J = C.jumps[idx];
@@ -234,7 +270,7 @@ void contract_point(const Contract &C, int g, std::vector<double> &grad, std::ve
         for (int a = 0; a < N; ++a)
             for (int b = 0; b < N; ++b) S[(size_t)a * N + b] = Ya[(size_t)a * N + b] + Ya[(size_t)b * N + a];
         // (M S)[a][b] = sum_e M[a][e] S[e][b] = sum_e M[a][e] S[b][e]
-        gram_rows(&Mall[(size_t)al * NN], S.data(), N, N, N, MS.data(), N);
+        rows_dot(&Mall[(size_t)al * NN], S.data(), N, N, N, MS.data(), N);
         for (int a = 0; a < N; ++a)
             for (int b = 0; b < N; ++b) Xa[(size_t)a * N + b] += MS[(size_t)a * N + b] - MS[(size_t)b * N + a];
     }
@@ -248,7 +284,7 @@ void contract_point(const Contract &C, int g, std::vector<double> &grad, std::ve
         }
     }
     // U[x][a] = sum_b V[x][b] W[a][b]
-    gram_rows(V, W.data(), D, N, N, U.data(), N);
+    rows_dot(V, W.data(), D, N, N, U.data(), N);
     std::vector<double> diagP(D, 0.0);
     double xsum = 0.0;  // sum_x sum_i P[x][x ^ 2^i]
     for (int x = 0; x < D; ++x) {

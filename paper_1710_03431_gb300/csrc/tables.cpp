@@ -335,8 +335,9 @@ aqt_status build_tables(const Inputs &in, Tables &tab, std::string *err) {
     double wmax = 10.0;
     for (int g = 0; g < K; ++g)
         wmax = std::max(wmax, tab.evals[(size_t)g * N + N - 1] - tab.evals[(size_t)g * N]);
-    Bath bath = in.bath;
-    bath.build_lamb(wmax * 1.05 + 1.0);
+    tab.bath = in.bath;
+    tab.bath.build_lamb(wmax * 1.05 + 1.0);
+    const Bath &bath = tab.bath;
 
     // ---- pass 2: manifolds, M_alpha, rates, H_eff ----------------------------
     parallel_for(K, [&](int g) {
