@@ -32,9 +32,10 @@ if ROOT not in sys.path:
 METRIC = "trajectory-steps/s"
 UNIT = "trajectory-steps/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes (read + write) of one propagate_tc launch, by workload (n, N, M, n_grid, t_f), from an ncu
-# capture of the kernel as it is now; empty until that capture is taken (then "traffic" is null).
-TC_TRAFFIC = {}
+# DRAM bytes (read + write) of one propagate_tc launch, by workload (n, N, M, n_grid, t_f), from a 1-pass
+# ncu capture of the kernel as it is now (dram__bytes_read.sum + dram__bytes_write.sum); a workload not
+# listed reports null.
+TC_TRAFFIC = {(8, 256, 10_000, 2000, 10.0): 565_135_872 + 18_879_744}
 
 def parse():
     ap = argparse.ArgumentParser()

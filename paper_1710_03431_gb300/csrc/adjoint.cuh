@@ -303,8 +303,8 @@ static __device__ __forceinline__ void load4(const double *p, double v[4]) {
 inline size_t back_smem_bytes(int N, int TT, size_t rs) {
     const int LD = TT + 4;
     const int KB = std::min(N, std::max(1, kChunkBytes / (int)(N * rs)));
-    return 2 * (size_t)N * 8 * 2           // level sums (im, re) and the span's conj decay (re, im)
-           + (size_t)N * 8                 // exp(2 Im K L)
+    return 2 * (size_t)N * 8               // level sums of jumped spans (im, re), FP64
+           + 6 * (size_t)N * rs            // level sums of the other spans, the span's conj decay, exp(2 Im K L)
            + 2 * (size_t)N * LD * rs       // adjoint tile
            + (size_t)KB * (N + 1) * rs     // transposed O chunk
            + 64;
@@ -318,10 +318,10 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
     const int TXN = TT / 4, TYN = kThreads / TXN;
     const int KB = min(N, max(1, kChunkBytes / (int)(N * sizeof(R))));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double *lsum = reinterpret_cast<double *>(smem);  // [N][2]: im, re
-    double *cd = lsum + 2 * N;                        // [N][2]: conj decay of the whole span
-    double *e2s = cd + 2 * N;                         // [N]
-    R *mre = reinterpret_cast<R *>(e2s + N);
+    double *lsum = reinterpret_cast<double *>(smem);  // [N][2]: im, re sums of the jumped spans (with 2 l)
+    R *lsumR = reinterpret_cast<R *>(lsum + 2 * N);   // [N][2]: im, re sums of mu^* c of the other spans
+    R *cdr = lsumR + 2 * N;                           // [N][2]: conj decay of the whole span, then [N] exp(2 Im K L)
+    R *mre = cdr + 4 * N;
     R *mim = mre + (size_t)N * LD;
     R *osm = mim + (size_t)N * LD;  // [KB][N + 1]
     const int64_t t0 = (int64_t)cta * TT;
@@ -359,10 +359,11 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
         for (int a = tid; a < N; a += kThreads) {
             double re, im, e2;
             cdecay(p, g, a, L, &re, &im, &e2);
-            cd[2 * a] = re;
-            cd[2 * a + 1] = im;
-            e2s[a] = e2;
+            cdr[2 * a] = (R)re;
+            cdr[2 * a + 1] = (R)im;
+            cdr[2 * N + a] = (R)e2;
             lsum[2 * a] = lsum[2 * a + 1] = 0.0;
+            lsumR[2 * a] = lsumR[2 * a + 1] = (R)0;
         }
         __syncthreads();
         // ---- the span of g, one warp per trajectory ----------------------------------
@@ -412,26 +413,28 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
                     mim[a * LD + t] = (R)mu[2 * a + 1];
                 }
             } else {
-                // no jump: mu_s = conj(D_L) mu_e / |D_L c_s|; mu^* c is the same at both ends
-                double s = 0.0;
+                // no jump: mu_s = conj(D_L) mu_e / |D_L c_s|; mu^* c is the same at both
+                // ends. In the state precision (the FP32 path's sums over a CTA's
+                // trajectories are FP32; across CTAs and steps FP64).
+                R s = (R)0;
                 if (g == 0) {
-                    s = e2s[0];
+                    s = cdr[2 * N];
                 } else {
                     for (int a = lane; a < N; a += 32) {
-                        const double re = cs[2 * a], im = cs[2 * a + 1];
-                        s += (re * re + im * im) * e2s[a];
+                        const R re = cs[2 * a], im = cs[2 * a + 1];
+                        s += (re * re + im * im) * cdr[2 * N + a];
                     }
                     s = warp_sum(s);
                 }
-                const double inv = 1.0 / sqrt(s);
+                const R inv = (R)1 / sqrt(s);
                 for (int a = lane; a < N; a += 32) {
-                    const double mr_ = mre[a * LD + t], mi_ = mim[a * LD + t];
-                    const double er = ce[2 * a], ei = ce[2 * a + 1];
-                    atomicAdd(&lsum[2 * a], 2.0 * L * (mr_ * ei - mi_ * er));
-                    atomicAdd(&lsum[2 * a + 1], 2.0 * L * (mr_ * er + mi_ * ei));
-                    const double dr = cd[2 * a], di = cd[2 * a + 1];
-                    mre[a * LD + t] = (R)((dr * mr_ - di * mi_) * inv);
-                    mim[a * LD + t] = (R)((dr * mi_ + di * mr_) * inv);
+                    const R mr_ = mre[a * LD + t], mi_ = mim[a * LD + t];
+                    const R er = ce[2 * a], ei = ce[2 * a + 1];
+                    atomicAdd(&lsumR[2 * a], mr_ * ei - mi_ * er);
+                    atomicAdd(&lsumR[2 * a + 1], mr_ * er + mi_ * ei);
+                    const R dr = cdr[2 * a], di = cdr[2 * a + 1];
+                    mre[a * LD + t] = (dr * mr_ - di * mi_) * inv;
+                    mim[a * LD + t] = (dr * mi_ + di * mr_) * inv;
                 }
             }
             __syncwarp();
@@ -442,8 +445,8 @@ __device__ __forceinline__ void back_tile(const RunParams &p, const AdjBack &b, 
         }
         __syncthreads();
         for (int a = tid; a < N; a += kThreads) {
-            atomicAdd(&b.lev[((size_t)g * N + a) * 2], lsum[2 * a]);
-            atomicAdd(&b.lev[((size_t)g * N + a) * 2 + 1], lsum[2 * a + 1]);
+            atomicAdd(&b.lev[((size_t)g * N + a) * 2], lsum[2 * a] + 2.0 * L * (double)lsumR[2 * a]);
+            atomicAdd(&b.lev[((size_t)g * N + a) * 2 + 1], lsum[2 * a + 1] + 2.0 * L * (double)lsumR[2 * a + 1]);
         }
         if (g == 0) break;
         // ---- frame rotation's adjoint: mu_e(g-1) = O_{g-1}^T mu_s(g) / |O c_e(g-1)| ------
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // points of a segment (start term for g >= 1, end term for g <= K - 2), FP64 out
 // [g][a][b]. One CTA per 64 x 64 output tile and grid point; 256 threads, 4 x 4
 // outputs each; trajectories in chunks of 8, summed in the state precision
-// within a chunk and in FP64 across chunks.
+// over 32 chunks and in FP64 across those.
 constexpr int kXT = 64, kXC = 8;
 
 template <typename R>
@@ -535,6 +538,12 @@ __global__ void __launch_bounds__(256) adj_xgemm(const R *seg_c, const R *seg_mu
     const R *ce = seg_c + ((size_t)gl * 2 + 1) * MN2, *cs = seg_c + ((size_t)gl * 2) * MN2;
     const R *me = seg_mu + ((size_t)gl * 2 + 1) * MN2, *ms = seg_mu + ((size_t)gl * 2) * MN2;
     double acc[4][4] = {};
+    R part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = (R)0;
+    int since = 0;
     for (int64_t t0 = 0; t0 < M; t0 += kXC) {
         __syncthreads();
         // 4 arrays x kXC trajectories x 128 values
@@ -549,11 +558,6 @@ __global__ void __launch_bounds__(256) adj_xgemm(const R *seg_c, const R *seg_mu
             if (w < 2) sa[w][t][v] = val; else sb[w - 2][t][v] = val;
         }
         __syncthreads();
-        R part[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) part[i][j] = (R)0;
 #pragma unroll
         for (int t = 0; t < kXC; ++t) {
 #pragma unroll
@@ -573,10 +577,17 @@ __global__ void __launch_bounds__(256) adj_xgemm(const R *seg_c, const R *seg_mu
                     for (int j = 0; j < 4; ++j) part[i][j] = fma(ar[i], br[j], fma(ai[i], bi[j], part[i][j]));
             }
         }
+        // FP64 every 32 chunks (256 trajectories x 4 terms in the state precision)
+        if (++since == 32 || t0 + kXC >= M) {
+            since = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j] += (double)part[i][j];
+                    part[i][j] = (R)0;
+                }
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)

@@ -220,14 +220,14 @@ __device__ __forceinline__ void simt_tile(const RunParams &p, int cta, double2 *
             if (t0 + t >= p.M) continue;
             R sc = (R)1;
             if (normalise) {
-                double nu = 0.0;
+                R nu = (R)0;
                 for (int a = lane; a < N; a += 32) {
-                    const double re = cre[a * LD + t], im = cim[a * LD + t];
+                    const R re = cre[a * LD + t], im = cim[a * LD + t];
                     nu += re * re + im * im;
                 }
                 nu = warp_sum(nu);
-                sc = (R)(1.0 / sqrt(nu));
-                if (lane == 0) adj.seg_nrot[(size_t)(g - g_begin) * p.M + t0 + t] = sqrt(nu);
+                sc = (R)1 / sqrt(nu);
+                if (lane == 0) adj.seg_nrot[(size_t)(g - g_begin) * p.M + t0 + t] = (double)sqrt(nu);
             }
             R *q = dst + (size_t)(t0 + t) * N * 2;
             for (int a = lane; a < N; a += 32) {

@@ -123,5 +123,6 @@ def test_autograd_function(aqt_lib):
     got = theta.grad.numpy()
     assert np.array_equal(np.isnan(got), np.isnan(g))
     ok = ~np.isnan(g)
-    # the per-level sums are FP64 atomics over CTAs (order not fixed): equal to rounding
-    np.testing.assert_allclose(got[ok], g[ok], rtol=1e-12, atol=1e-15)
+    # the per-level sums are atomics (FP32 within a CTA, FP64 across CTAs) whose
+    # order is not fixed: equal to FP32 rounding
+    np.testing.assert_allclose(got[ok], g[ok], rtol=1e-5, atol=1e-9)
