@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "aqt_internal.h"
 #include "device_jump.cuh"
@@ -517,45 +518,55 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // X_g = 2 sum over trajectories [Re(mu_e^* c_e^T) - Re(mu_s^* c_s^T)] for the grid
-// points of a segment (start term for g >= 1, end term for g <= K - 2), FP64 out
-// [g][a][b]. One CTA per 64 x 64 output tile and grid point; 256 threads, 4 x 4
-// outputs each; trajectories in chunks of 8, summed in the state precision
-// over 32 chunks and in FP64 across those.
-constexpr int kXT = 64, kXC = 8;
+// points of a segment (start term for g >= 1, end term for g <= K - 2), added
+// into FP64 xout [g][a][b] (zeroed before the first segment). One CTA per
+// 128 x 128 output tile, grid point and block of kXM trajectories; 256
+// threads, each 8 x 8 outputs: levels a0 + 4 ty + i and a0 + 64 + 4 ty + i (and
+// the same for b with tx), so that a quarter-warp's operand loads fall on
+// distinct banks but pairs; trajectories in chunks staged in shared memory,
+// summed in the state precision over the block, then added in FP64 (atomics
+// across the blocks).
+constexpr int kXT = 128, kXM = 2048;
 
 template <typename R>
 __global__ void __launch_bounds__(256) adj_xgemm(const R *seg_c, const R *seg_mu, int64_t M, int N, int K,
                                                  int g_begin, double *xout) {
+    constexpr int kXC = 16 / sizeof(R) * 2;  // trajectories per staged chunk: 8 (FP32), 4 (FP64)
+    constexpr int V = 16 / sizeof(R);        // values per 16-byte vector
+    typedef typename std::conditional<sizeof(R) == 4, float4, double2>::type vec;
     __shared__ __align__(16) R sa[2][kXC][2 * kXT];  // mu_e, mu_s
     __shared__ __align__(16) R sb[2][kXC][2 * kXT];  // c_e, c_s
     const int tiles = N / kXT;
     const int gl = blockIdx.y;
     const int g = g_begin + gl;
     const int a0 = (blockIdx.x / tiles) * kXT, b0 = (blockIdx.x % tiles) * kXT;
+    const int64_t m0 = (int64_t)blockIdx.z * kXM, m1 = min(M, m0 + kXM);
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const bool has_e = g <= K - 2, has_s = g >= 1;
     const size_t MN2 = (size_t)M * N * 2;
     const R *ce = seg_c + ((size_t)gl * 2 + 1) * MN2, *cs = seg_c + ((size_t)gl * 2) * MN2;
     const R *me = seg_mu + ((size_t)gl * 2 + 1) * MN2, *ms = seg_mu + ((size_t)gl * 2) * MN2;
-    double acc[4][4] = {};
-    R part[4][4];
+    R acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) part[i][j] = (R)0;
-    int since = 0;
-    for (int64_t t0 = 0; t0 < M; t0 += kXC) {
+        for (int j = 0; j < 8; ++j) acc[i][j] = (R)0;
+    for (int64_t t0 = m0; t0 < m1; t0 += kXC) {
         __syncthreads();
-        // 4 arrays x kXC trajectories x 128 values
-        for (int i = tid; i < 4 * kXC * 2 * kXT; i += 256) {
-            const int w = i / (kXC * 2 * kXT), r = i % (kXC * 2 * kXT);
-            const int t = r / (2 * kXT), v = r % (2 * kXT);
+        // 4 arrays x kXC trajectories x 2 kXT values, as 16-byte vectors
+        constexpr int per = 2 * kXT / V;  // vectors per trajectory row
+        for (int i = tid; i < 4 * kXC * per; i += 256) {
+            const int w = i / (kXC * per), r = i % (kXC * per);
+            const int t = r / per, v = r % per;
             const int64_t tr = t0 + t;
             const int lev0 = (w < 2 ? a0 : b0);
             const R *src = w == 0 ? me : w == 1 ? ms : w == 2 ? ce : cs;
-            const bool on = tr < M && ((w % 2 == 0) ? has_e : has_s);
-            const R val = on ? src[(size_t)tr * N * 2 + 2 * lev0 + v] : (R)0;
-            if (w < 2) sa[w][t][v] = val; else sb[w - 2][t][v] = val;
+            const bool on = tr < m1 && ((w % 2 == 0) ? has_e : has_s);
+            vec val;
+            if (on) val = *reinterpret_cast<const vec *>(src + (size_t)tr * N * 2 + 2 * lev0 + V * v);
+            else val = vec{};
+            R *dst = w < 2 ? &sa[w][t][V * v] : &sb[w - 2][t][V * v];
+            *reinterpret_cast<vec *>(dst) = val;
         }
         __syncthreads();
 #pragma unroll
@@ -563,40 +574,45 @@ __global__ void __launch_bounds__(256) adj_xgemm(const R *seg_c, const R *seg_mu
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const R sg = e == 0 ? (R)1 : (R)-1;
-                R ar[4], ai[4], br[4], bi[4];
+                R ar[8], ai[8], br[8], bi[8];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ar[i] = sg * sa[e][t][2 * (4 * ty + i)];
-                    ai[i] = sg * sa[e][t][2 * (4 * ty + i) + 1];
-                    br[i] = sb[e][t][2 * (4 * tx + i)];
-                    bi[i] = sb[e][t][2 * (4 * tx + i) + 1];
+                for (int h = 0; h < 2; ++h) {
+                    const R *pa = &sa[e][t][2 * (64 * h + 4 * ty)];
+                    const R *pb = &sb[e][t][2 * (64 * h + 4 * tx)];
+                    R va[8], vb[8];
+#pragma unroll
+                    for (int q = 0; q < 8 / V; ++q) {
+                        *reinterpret_cast<vec *>(&va[V * q]) = *reinterpret_cast<const vec *>(pa + V * q);
+                        *reinterpret_cast<vec *>(&vb[V * q]) = *reinterpret_cast<const vec *>(pb + V * q);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ar[4 * h + i] = sg * va[2 * i];
+                        ai[4 * h + i] = sg * va[2 * i + 1];
+                        br[4 * h + i] = vb[2 * i];
+                        bi[4 * h + i] = vb[2 * i + 1];
+                    }
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) part[i][j] = fma(ar[i], br[j], fma(ai[i], bi[j], part[i][j]));
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fma(ar[i], br[j], fma(ai[i], bi[j], acc[i][j]));
             }
-        }
-        // FP64 every 32 chunks (256 trajectories x 4 terms in the state precision)
-        if (++since == 32 || t0 + kXC >= M) {
-            since = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[i][j] += (double)part[i][j];
-                    part[i][j] = (R)0;
-                }
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i) {
+        const int a = a0 + 64 * (i >> 2) + 4 * ty + (i & 3);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            xout[((size_t)g * N + a0 + 4 * ty + i) * N + b0 + 4 * tx + j] = 2.0 * acc[i][j];
+        for (int j = 0; j < 8; ++j) {
+            const int b = b0 + 64 * (j >> 2) + 4 * tx + (j & 3);
+            atomicAdd(&xout[((size_t)g * N + a) * N + b], 2.0 * (double)acc[i][j]);
+        }
+    }
 }
 
-// The same for N < 64: one thread per output entry, FP64 accumulation.
+// The same for other N (not a multiple of 128): one thread per output entry,
+// FP64 accumulation, written (not added).
 template <typename R>
 __global__ void __launch_bounds__(256) adj_xgemm_small(const R *seg_c, const R *seg_mu, int64_t M, int N, int K,
                                                        int g_begin, double *xout) {
@@ -643,7 +659,7 @@ template <typename R>
 int launch_xgemm(const void *seg_c, const void *seg_mu, int64_t M, int N, int K, int g_begin, int n_g, double *xout,
                  cudaStream_t st) {
     if (N % kXT == 0) {
-        dim3 grid((N / kXT) * (N / kXT), n_g);
+        dim3 grid((N / kXT) * (N / kXT), n_g, (unsigned)((M + kXM - 1) / kXM));
         adj_xgemm<R><<<grid, 256, 0, st>>>(reinterpret_cast<const R *>(seg_c), reinterpret_cast<const R *>(seg_mu), M,
                                            N, K, g_begin, xout);
     } else {

@@ -494,6 +494,7 @@ aqt_status aqt_grad_backward(aqt_ctx *c, double baseline, void *stream) {
     int ce = 0;
     cudaError_t e = cudaMemsetAsync(w + G->lev, 0, (size_t)K * N * 2 * 8, st);
     if (!e) e = cudaMemsetAsync(w + G->jout_n, 0, 8, st);
+    if (!e) e = cudaMemsetAsync(w + G->xout, 0, (size_t)K * N * N * 8, st);  // the outer products add into it
     if (e) return set_error(c, AQT_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     // ---- segments, last first -----------------------------------------------------------
     for (int sgi = G->n_seg - 1; sgi >= 0; --sgi) {

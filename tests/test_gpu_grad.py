@@ -60,6 +60,33 @@ def test_fp64_gradient_matches_record_replay(aqt_lib, every):
     np.testing.assert_allclose(g[~und], ref[~und], rtol=1e-6, atol=1e-7 * scale)
 
 
+def test_tiled_outer_products_identity_and_segments(aqt_lib):
+    """N = 128: the outer products run on the tiled kernel (128 x 128 tiles,
+    trajectories split over blocks and added in FP64). The field-scaling
+    identity holds per trajectory, so the sum over trajectories checks the
+    tiled sums through every parameter class; two checkpoint spacings give
+    the same gradient to rounding."""
+    A = aqt_lib
+    inst = W.tfim_instance(7, 3, eta_g2=0.05, t_f=2.0, n_grid=40, seed=5, M=2100)
+    g1, _, j1 = device_grad(A, inst, A.AQT_PREC_FP64, 0.5, 7)
+    g2, _, j2 = device_grad(A, inst, A.AQT_PREC_FP64, 0.5, 64)
+    assert len(j1) == len(j2) > 100
+    th = G.param_vector(inst)
+    k = len(inst.sched_s)
+    for g in (g1, g2):
+        lhs = np.dot(th[2 * k:], g[2 * k:])
+        rhs = np.nansum(th[k:2 * k] * np.where(np.isnan(g[k:2 * k]), 0.0, g[k:2 * k]))
+        assert abs(lhs - rhs) <= 1e-9 * max(1.0, abs(lhs)), (lhs, rhs)
+    ok = ~np.isnan(g1)
+    assert np.array_equal(ok, ~np.isnan(g2))
+    np.testing.assert_allclose(g1[ok], g2[ok], rtol=1e-9, atol=1e-12 * np.max(np.abs(g1[ok])))
+    # the FP32 form of the tiled kernel (state-precision sums over blocks of 2048 trajectories)
+    g32, _, j32 = device_grad(A, inst, A.AQT_PREC_FP32, 0.5, 16)
+    scale = np.max(np.abs(g1[ok]))
+    tol = (2e-4 if len(j32) == len(j1) else 2e-2) * scale
+    assert np.max(np.abs(g32[ok] - g1[ok])) <= tol, (g32, g1)
+
+
 def test_field_scaling_identity_on_device(aqt_lib):
     A = aqt_lib
     inst = hot(n=4, seed=9, K=50, M=256)
