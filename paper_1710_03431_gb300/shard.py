@@ -58,3 +58,21 @@ def gather_jumps(jumps: np.ndarray, M_local: int, group=None):
     allj = np.concatenate(parts) if parts else mine
     order = np.lexsort((allj["t"], allj["traj"]))
     return allj[order]
+
+
+def merge_gradient(grad, M_local: int, group=None, device=None):
+    """The gradient of the merged ensemble from the ranks' gradients (each the
+    mean over its own M_r trajectories, aqt_grad_get): one all-reduce (sum) of
+    M_r grad_r and M_r; the merged value is their ratio. A parameter without a
+    derivative (NaN) stays NaN. Returns (grad, M_total)."""
+    import torch
+    import torch.distributed as dist
+    g = np.asarray(grad, dtype=np.float64)
+    buf = torch.empty(len(g) + 1, dtype=torch.float64, device=device)
+    buf[:len(g)] = torch.as_tensor(g * float(M_local))
+    buf[len(g)] = float(M_local)
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    out = buf.cpu().numpy()
+    M = out[len(g)]
+    return out[:len(g)] / M, int(round(M))
+

@@ -1,7 +1,7 @@
 """The multi-rank path on CPU (gloo, world size 2): trajectories shard across
 ranks with one Philox key per rank; the bench takes the maximum of the ranks'
 timed regions, and the one exchange of results (observable sums, jump
-records) merges the ranks' trajectories into one ensemble."""
+records, gradients) merges the ranks' trajectories into one ensemble."""
 import os
 import socket
 
@@ -88,4 +88,42 @@ def test_two_ranks_merge_observables_and_jumps(aqt_lib):
     assert len(res[0][4]) == len(own0) + len(own1) > 0
     assert np.array_equal(res[0][4], res[1][4])
     assert set(res[0][4]["traj"].tolist()) == set(own0["traj"].tolist()) | {t + 6 for t in own1["traj"].tolist()}
+
+
+def _grad_rank(rank, world, port, out):
+    import torch.distributed as dist
+
+    import workloads as W
+    from oracle import gradient as G
+    from oracle import trajectories
+    from paper_1710_03431_gb300 import shard
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inst = W.tfim_instance(2, 3, eta_g2=0.05, t_f=4.0, n_grid=6, seed=7, lamb_shift=False)
+        M = 2 + rank  # uneven shards
+        seed = shard.rank_seed(inst.seed, rank)
+        p, jumps, _ = trajectories.sample(inst, list(range(M)), seed=seed)
+        per = [G.trajectory_gradient_fd(inst, [j for j in jumps if j["traj"] == t], baseline=0.5)[0]
+               for t in range(M)]
+        g, Mt = shard.merge_gradient(np.mean(per, axis=0), M)
+        out[rank] = (np.array(per), g, Mt)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_merge_gradients():
+    """The merged gradient is the mean of the per-trajectory estimates of both
+    ranks' trajectories (uneven shards), NaN where a parameter has none."""
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.start_processes(_grad_rank, args=(2, port, out), nprocs=2, start_method="spawn")
+        res = dict(out)
+    allper = np.concatenate([res[0][0], res[1][0]])
+    ref = allper.mean(axis=0)
+    for r in (0, 1):
+        _, g, Mt = res[r]
+        assert Mt == len(allper) == 5
+        np.testing.assert_allclose(g, ref, rtol=1e-13, atol=1e-15)
 
