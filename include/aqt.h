@@ -374,7 +374,7 @@ aqt_status aqt_batch_get_shape(aqt_batch *batch, int member, int32_t *shape);
  * grid point (at s = 0 of the transverse-field model: B at the first knot)
  * has no derivative in the secular AME (the Bohr classes of Eq. Lindblad2
  * regroup as the degeneracy lifts): its entry is NaN. */
-aqt_status aqt_grad_n_params(aqt_ctx *ctx, int *n_params);
+aqt_status aqt_grad_n_params(aqt_ctx *ctx, int *n_params);  /* needs the inputs only (any context) */
 
 /* Device bytes of a gradient run for the current inputs (a second workspace,
  * beside aqt_workspace_size's): checkpoints every checkpoint_every grid points

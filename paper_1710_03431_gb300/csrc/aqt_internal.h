@@ -358,6 +358,8 @@ struct GradAccess {
 };
 aqt_status grad_access(aqt_ctx *ctx, GradAccess *a, bool need_device_tables);
 GradState *grad_state_get(aqt_ctx *ctx);
+// The context's inputs once every set_* call has been made, else null (no device needed).
+const Inputs *ctx_inputs(const aqt_ctx *ctx);
 void grad_state_set(aqt_ctx *ctx, GradState *g);
 void grad_mark_ran(aqt_ctx *ctx, void *stream);
 aqt_status static_run_params(aqt_ctx *ctx, RunParams *p);

@@ -301,6 +301,8 @@ aqt_status grad_access(aqt_ctx *c, GradAccess *a, bool need_device_tables) {
 
 GradState *grad_state_get(aqt_ctx *c) { return c->grad; }
 
+const Inputs *ctx_inputs(const aqt_ctx *c) { return inputs_complete(c) ? &c->in : nullptr; }
+
 void grad_state_set(aqt_ctx *c, GradState *g) {
     grad_free(c->grad);
     c->grad = g;

@@ -405,10 +405,9 @@ extern "C" {
 
 aqt_status aqt_grad_n_params(aqt_ctx *c, int *n_params) {
     if (!c || !n_params) return AQT_EINVAL;
-    GradAccess A;
-    aqt_status s = grad_access(c, &A, false);
-    if (s != AQT_OK) return s;
-    *n_params = n_params_of(*A.in);
+    const Inputs *in = ctx_inputs(c);
+    if (!in) return set_error(c, AQT_EINVAL, "set all inputs first");
+    *n_params = n_params_of(*in);
     return AQT_OK;
 }
 

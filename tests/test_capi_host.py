@@ -289,3 +289,30 @@ def test_dt_condition_terms_and_warning(aqt_lib):
     assert A.aqt_build_tables(c, 0) == A.AQT_WDT
     assert "newcond" in A.aqt_last_error(c)
     A.aqt_destroy(c)
+
+
+def test_gradient_entry_points_on_a_host_context(aqt_lib):
+    """The parameter count needs the inputs only; the device calls of a
+    gradient run refuse a host-only context."""
+    A = aqt_lib
+    inst = W.tfim_instance(3, 5, t_f=2.0, n_grid=20, M=8, seed=3)
+    c = _host_ctx(A, inst, M=8)
+    try:
+        k = len(inst.sched_s)
+        assert A.aqt_grad_n_params(c) == 2 * k + 3 + 3
+        with pytest.raises(A.AqtError) as e:
+            A.aqt_grad_workspace_size(c, 64, 1024)
+        assert e.value.status == A.AQT_ENODEV
+        with pytest.raises(A.AqtError) as e:
+            A.aqt_grad_forward(c, 0)
+        assert e.value.status == A.AQT_ENODEV
+    finally:
+        A.aqt_destroy(c)
+    c = A.aqt_create(-1)
+    try:
+        with pytest.raises(A.AqtError) as e:
+            A.aqt_grad_n_params(c)
+        assert e.value.status == A.AQT_EINVAL
+    finally:
+        A.aqt_destroy(c)
+
