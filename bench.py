@@ -34,8 +34,8 @@ UNIT = "trajectory-steps/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes (read + write) of one propagate_tc launch, by workload (n, N, M, n_grid, t_f), from a 1-pass
 # ncu capture of the kernel as it is now (dram__bytes_read.sum + dram__bytes_write.sum); a workload not
-# listed reports null.
-TC_TRAFFIC = {(8, 256, 10_000, 2000, 10.0): 565_135_872 + 18_879_744}
+# listed, or a kernel changed since its capture, reports null.
+TC_TRAFFIC = {}
 
 def parse():
     ap = argparse.ArgumentParser()
