@@ -369,7 +369,7 @@ aqt_status aqt_batch_get_shape(aqt_batch *batch, int member, int32_t *shape);
  * jump operators.
  *
  * Scope: AQT_PREC_FP64 or AQT_PREC_FP32, AQT_JUMP_REFINED, every level kept
- * (no aqt_set_levels), at most 9 qubits; otherwise AQT_EINVAL. A parameter
+ * (no aqt_set_levels), at most 8 qubits; otherwise AQT_EINVAL. A parameter
  * whose dH_S/dtheta couples two levels of one degenerate manifold at some
  * grid point (at s = 0 of the transverse-field model: B at the first knot)
  * has no derivative in the secular AME (the Bohr classes of Eq. Lindblad2

@@ -113,7 +113,7 @@ aqt_status check_inputs(aqt_ctx *c, const GradAccess &A) {
         return set_error(c, AQT_EINVAL, "gradient runs take AQT_PREC_FP64 or AQT_PREC_FP32");
     if (in.timing != AQT_JUMP_REFINED) return set_error(c, AQT_EINVAL, "gradient runs take AQT_JUMP_REFINED timing");
     if (in.levels() != (1 << in.n)) return set_error(c, AQT_EINVAL, "gradient runs keep every level (no aqt_set_levels)");
-    if (in.levels() > 512) return set_error(c, AQT_EINVAL, "gradient runs take at most 9 qubits");
+    if (in.levels() > 256) return set_error(c, AQT_EINVAL, "gradient runs take at most 8 qubits");
     return AQT_OK;
 }
 
