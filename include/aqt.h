@@ -380,15 +380,16 @@ aqt_status aqt_grad_n_params(aqt_ctx *ctx, int *n_params);  /* needs the inputs 
  * beside aqt_workspace_size's): checkpoints every checkpoint_every grid points
  * ([n_grid / checkpoint_every] x M x N states), one segment's states and
  * adjoints (4 x checkpoint_every x M x N), the per-grid-point sums
- * (n_grid x N x N FP64) and room for jump_capacity jumps of the whole run
- * (2 x N FP64 vectors each). Builds the host tables if needed. */
+ * (n_grid x N x N FP64), 16 jump slots per trajectory for one segment and
+ * room for jump_capacity jumps of the whole run (2 x N FP64 vectors each).
+ * Builds the host tables if needed. */
 aqt_status aqt_grad_workspace_size(aqt_ctx *ctx, int checkpoint_every, int64_t jump_capacity, size_t *bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, at least
  * aqt_grad_workspace_size bytes for the same checkpoint_every and
  * jump_capacity) for gradient runs. It must stay allocated while the context
  * uses it; the library never frees it. Changing any set_* input invalidates
- * it (aqt_grad_run then returns AQT_EINVAL). */
+ * it (aqt_grad_forward and aqt_grad_backward then return AQT_EINVAL). */
 aqt_status aqt_grad_bind_workspace(aqt_ctx *ctx, int checkpoint_every, int64_t jump_capacity, void *dptr,
                                    size_t bytes);
 
